@@ -1,0 +1,262 @@
+/*
+ * svt.h -- C ABI of libsvt: singular value soft-thresholding without an SVD,
+ * on one GB300 GPU (sm_103a).
+ *
+ * What it computes (Becker, "Singular value soft-thresholding via the polar
+ * decomposition"):
+ *
+ *   Eq. 1:           A_tau = U max(Sigma - tau I, 0) V^T
+ *   Proposition 1:   A_tau = 1/2 (A + A S) - tau/2 (P + P S)
+ *                    with P = polar(A), S = polar(A^T A - tau^2 I)
+ *   (factored form)  A_tau = 1/2 (A - tau P)(I + S)
+ *   Footnote:        for n > m, S = polar(A A^T - tau^2 I) and
+ *                    A_tau = 1/2 (I + S)(A - tau P)
+ *
+ * The shift is tau^2 (the paper's code listing, Section 4); the proposition as
+ * printed writes tau I, which does not split the spectrum at sigma = tau.
+ * P and S are computed by odd-polynomial polar iterations that use only matrix
+ * products (Section 1: Newton-Schulz; Section 3: Polar Express), on tensor cores.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are row-major FP32 in DEVICE memory; element (i, j) of an m x n
+ *     matrix with leading dimension ld is at ptr[i * ld + j]; ld >= n.
+ *   - The caller owns every buffer it passes (A, Y, workspace, status words).
+ *     The library never frees caller memory and allocates no device memory on
+ *     any solve path; all scratch lives in the workspace given to
+ *     svt_ctx_create.
+ *   - Argument errors are returned synchronously (SVT_ERR_INVALID) before any
+ *     launch, like the paper's ValueError on non-2-D input (Section 4).
+ *   - Errors found on the device (non-finite input, divergence, a device wait
+ *     that ran out of time) are written to the caller's device status word
+ *     (svt_status, 4 bytes) when one is given, and are returned by
+ *     svt_ctx_sync / svt_serve_poll.
+ *   - Streams are cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - A context is not thread-safe, except svt_serve_submit / svt_serve_poll,
+ *     which may be called from any thread.
+ */
+#ifndef SVT_H
+#define SVT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SVT_OK = 0,
+    SVT_ERR_INVALID = 1,   /* bad argument (null pointer, size, ld, tau, iters) */
+    SVT_ERR_OOM = 2,       /* workspace or admission budget too small */
+    SVT_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    SVT_ERR_NONFINITE = 4, /* input contains NaN or Inf (found on the device) */
+    SVT_ERR_DIVERGED = 5,  /* iteration produced a non-finite value */
+    SVT_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
+    SVT_ERR_NOT_READY = 7, /* serving ticket still pending */
+    SVT_ERR_BUSY = 8,      /* serving queue full */
+    SVT_ERR_UNSUPPORTED = 9 /* size or option outside what this build supports */
+} svt_status;
+
+typedef enum {
+    SVT_FP64 = 0, /* every step in FP64 (SIMT); correctness tier, small inputs */
+    SVT_FP32 = 1, /* every product FP32-class: three BF16 tensor-core products
+                     (hi*hi + hi*lo + lo*hi) with FP32 accumulation */
+    SVT_BF16 = 2  /* polynomial steps in BF16 (FP32 accumulation); Gram, polish
+                     and combine FP32-class; norms and the tau^2 shift in FP64 */
+} svt_precision;
+
+typedef enum {
+    SVT_SCHED_AUTO = 0, /* PE5 */
+    SVT_SCHED_PE5 = 1,  /* Polar-Express-style minimax odd quintics (Section 3) */
+    SVT_SCHED_NS3 = 2   /* cubic Newton-Schulz X (3/2 I - 1/2 X^T X) (Section 1) */
+} svt_schedule_kind;
+
+typedef enum {
+    SVT_NORM_AUTO = 0, /* GRAM for PE5, FRO for NS3 */
+    SVT_NORM_FRO = 1,  /* divide the chain's start by its Frobenius norm */
+    SVT_NORM_GRAM = 2  /* divide by ||X0^T X0||_F^(1/2) (>= ||X0||_2, tighter) */
+} svt_norm_kind;
+
+typedef enum {
+    SVT_MODE_SVT = 0,    /* A_tau (Proposition 1) */
+    SVT_MODE_RANK_R = 1  /* Corollary 1: 1/2 (A + A S), the best rank-r
+                            approximation when tau lies between sigma_{r+1}
+                            and sigma_r; the P chain is skipped */
+} svt_mode;
+
+/* Per-solve options. svt_options_default fills the defaults noted here. */
+typedef struct {
+    int iters;                  /* polynomial steps per chain, >= 0 (default 20) */
+    svt_precision prec;         /* default SVT_BF16 */
+    svt_schedule_kind schedule; /* default SVT_SCHED_AUTO */
+    svt_norm_kind norm;         /* default SVT_NORM_AUTO */
+    double ell0;                /* PE5 lower end of the first interval, in (0,1)
+                                   (default 1e-3) */
+    double delta;               /* PE5 interval widening (default: 0.01 BF16,
+                                   1e-4 FP32, 0 FP64); < 0 selects the default */
+    int polish;                 /* 1: one cubic Newton-Schulz step per chain in
+                                   the FP32-class tier after the iterations
+                                   (default 1; ignored for SVT_FP64, which
+                                   polishes in FP64) */
+    svt_mode mode;              /* default SVT_MODE_SVT */
+} svt_options;
+
+typedef struct svt_ctx *svt_ctx_t;
+
+/* One matrix of a batch or one serving request. */
+typedef struct {
+    const float *A;      /* m x n device, row-major, leading dimension lda */
+    int64_t m, n, lda;
+    float tau;           /* threshold, finite, >= 0 */
+    float *Y;            /* m x n device output, leading dimension ldy */
+    int64_t ldy;
+    svt_options opt;     /* per-matrix options */
+    svt_status *d_status; /* nullable device status word for this matrix */
+} svt_matrix;
+
+/* Human-readable name of a status code. Never NULL. */
+const char *svt_status_str(svt_status s);
+
+/* Fill *opt with the defaults documented in svt_options. */
+void svt_options_default(svt_options *opt);
+
+/*
+ * Device workspace one solve of an m x n matrix needs (bytes), for the given
+ * options (NULL = defaults). Pure host arithmetic.
+ * Errors: SVT_ERR_INVALID on m, n <= 0 or out == NULL.
+ */
+svt_status svt_workspace_bytes_ex(int64_t m, int64_t n, const svt_options *opt, size_t *out);
+
+/* Same with default options and the given precision. */
+svt_status svt_workspace_bytes(int64_t m, int64_t n, svt_precision prec, size_t *out);
+
+/*
+ * Create a context on CUDA device `device` that uses the caller's device buffer
+ * `workspace` (ws_bytes bytes, 256-byte aligned) for all scratch. The context
+ * creates two CUDA streams and a few events and keeps a cache of launch plans;
+ * it allocates no device memory.
+ * Errors: SVT_ERR_INVALID (null out, misaligned or null workspace with
+ * ws_bytes > 0), SVT_ERR_CUDA.
+ */
+svt_status svt_ctx_create(int device, void *workspace, size_t ws_bytes, svt_ctx_t *out);
+
+/* Stop the serving thread (if started), wait for the context's streams and free
+ * the context's host state. The workspace stays the caller's. */
+svt_status svt_ctx_destroy(svt_ctx_t ctx);
+
+/*
+ * svt_polar: Y = A_tau for one m x n matrix, enqueued on `stream`.
+ *   A: m x n FP32 device (lda >= n), read only.  Y: m x n FP32 device (ldy >= n).
+ *   A and Y must not overlap. tau: finite, >= 0. iters >= 0.
+ *   prec: precision tier (see svt_precision); other options at their defaults.
+ *   d_status: nullable device word; receives SVT_OK or a device-side error.
+ * Branch: m >= n uses A^T A (n x n Gram); n > m uses A A^T (footnote), computed
+ * as the tall problem of A^T with the result transposed back.
+ * Returns SVT_OK once all work is enqueued (asynchronous), or a synchronous
+ * error: SVT_ERR_INVALID, SVT_ERR_OOM (workspace too small),
+ * SVT_ERR_UNSUPPORTED (SVT_FP64 above 4096 in either dimension), SVT_ERR_CUDA.
+ */
+svt_status svt_polar(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int64_t lda,
+                     float tau, int iters, svt_precision prec, float *Y, int64_t ldy,
+                     svt_status *d_status, void *stream);
+
+/* svt_polar with explicit options (NULL = defaults). Same contract. */
+svt_status svt_polar_ex(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int64_t lda,
+                        float tau, const svt_options *opt, float *Y, int64_t ldy,
+                        svt_status *d_status, void *stream);
+
+/*
+ * svt_batch: A_tau for `count` independent matrices of any sizes, enqueued on
+ * `stream`. All matrices advance together: every stage of every matrix (both
+ * chains) goes out as one grouped persistent launch, and the launch sequence is
+ * captured once per batch shape signature into a CUDA graph and replayed.
+ * The workspace must hold the sum of the matrices' workspaces
+ * (svt_batch_workspace_bytes).
+ * Errors: as svt_polar, checked for every matrix before any launch.
+ */
+svt_status svt_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, void *stream);
+
+/* Workspace bytes svt_batch needs for these matrices. */
+svt_status svt_batch_workspace_bytes(const svt_matrix *mats, int count, size_t *out);
+
+/*
+ * Serving (continuous batching). svt_serve_submit copies the request descriptor
+ * (A and Y stay caller-owned device memory and must stay valid until the ticket
+ * completes) into the admission queue and returns a ticket. A scheduler thread
+ * admits queued requests while their workspaces fit in the context's workspace
+ * and a slot is free, advances all admitted requests one stage window at a time
+ * with one grouped launch per window, and retires finished requests.
+ * Errors: SVT_ERR_INVALID (bad request), SVT_ERR_OOM (request larger than the
+ * whole workspace), SVT_ERR_BUSY (queue full).
+ */
+svt_status svt_serve_submit(svt_ctx_t ctx, const svt_matrix *req, uint64_t *ticket);
+
+/*
+ * Poll a ticket: SVT_ERR_NOT_READY while pending; otherwise the request's final
+ * status (SVT_OK or the device-side error), with the submit-to-completion
+ * latency in milliseconds in *latency_ms (nullable). A completed ticket can be
+ * polled again until svt_serve_release.
+ */
+svt_status svt_serve_poll(svt_ctx_t ctx, uint64_t ticket, double *latency_ms);
+
+/* Forget a completed ticket. SVT_ERR_NOT_READY if still pending. */
+svt_status svt_serve_release(svt_ctx_t ctx, uint64_t ticket);
+
+/* Wait for all work of the context (svt_polar/svt_batch streams and serving)
+ * and return the first device-side error recorded since the last sync. */
+svt_status svt_ctx_sync(svt_ctx_t ctx, void *stream);
+
+/*
+ * The polynomial schedule the library uses (host arithmetic, no GPU):
+ * coefficients (a_t, b_t, c_t) of p_t(x) = a x + b x^3 + c x^5 for t < iters,
+ * written to coef[3 t .. 3 t + 2]. kind SVT_SCHED_NS3 gives (1.5, -0.5, 0).
+ * PE5: each p_t minimises max |1 - p(x)| over [l_t, (1 + delta) u_t] (Remez),
+ * [l_0, u_0] = [ell0, 1], and the next interval is [1 - E_t, 1 + E_t]; once the
+ * design interval is narrower than 1e-3 the step is (15/8, -5/4, 3/8).
+ * Errors: SVT_ERR_INVALID (iters < 0, coef NULL with iters > 0, ell0 not in (0,1),
+ * delta < 0).
+ */
+svt_status svt_schedule_coeffs(svt_schedule_kind kind, int iters, double ell0, double delta,
+                               double *coef);
+
+/*
+ * Diagnostic entry point for the tensor-core product kernel (used by the tests):
+ *   D = sum_s L_s R_s^T with nseg in {1, 2, 3} segments taken from hi/lo parts:
+ *     nseg 1: L_hi R_hi^T
+ *     nseg 2: L_hi R_hi^T + L_hi R_lo^T
+ *     nseg 3: L_hi R_hi^T + L_hi R_lo^T + L_lo R_hi^T
+ *   L parts are M x K BF16 row-major (leading dimension ldl), R parts N x K BF16
+ *   row-major (ldr); ldl and ldr multiples of 8, device pointers 16-byte
+ *   aligned, unused parts may be NULL. FP32 accumulation in tensor memory; D is
+ *   written as FP32 row-major (ldd >= N). sym = 1 computes only the tiles on or
+ *   above the diagonal and mirrors them (requires M == N).
+ * Errors: SVT_ERR_INVALID, SVT_ERR_CUDA.
+ */
+svt_status svt_debug_gemm_bf16(svt_ctx_t ctx, int nseg, const void *L_hi, const void *L_lo,
+                               const void *R_hi, const void *R_lo, int64_t M, int64_t N,
+                               int64_t K, int64_t ldl, int64_t ldr, float *D, int64_t ldd,
+                               int sym, void *stream);
+
+/* Number of kernel launches the library has issued on this context so far
+ * (host counter; used to report launches per solve). */
+uint64_t svt_ctx_launch_count(svt_ctx_t ctx);
+
+/*
+ * Measurement hooks. svt_ctx_profile(ctx, 1) makes every later tensor-core
+ * launch of svt_polar / svt_polar_ex on this context record a CUDA event pair
+ * on its own stream (0 turns it off; both reset the record).
+ * svt_ctx_profile_read waits for the recorded events and returns, since the last
+ * reset, the summed device time of those launches (ms), their summed
+ * algorithmic flops (2 M N K per product, symmetric products counted at half,
+ * hi/lo segments of FP32-class products not counted again) and their number;
+ * then resets. Errors: SVT_ERR_INVALID (null argument), SVT_ERR_CUDA.
+ */
+svt_status svt_ctx_profile(svt_ctx_t ctx, int enable);
+svt_status svt_ctx_profile_read(svt_ctx_t ctx, double *tc_ms, double *tc_flops,
+                                uint64_t *tc_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVT_H */

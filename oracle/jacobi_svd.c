@@ -75,12 +75,15 @@ static int rotate_pair(double *W, double *V, int64_t m, int64_t n, int64_t p, in
  *   eps       : orthogonality tolerance; <= 0 selects m * 2^-53.
  *   max_sweeps: sweep limit (the result is returned even if not converged).
  *   nthreads  : OpenMP threads (<= 0 keeps the runtime default).
- *   sweeps_out: number of sweeps run; off_out: max |gamma|/sqrt(alpha beta) seen
- *               in the last sweep (0 when converged on the first pass of it).
- * Returns 0 when converged, 1 when the sweep limit was hit, -1 on bad arguments.
+ *   max_rounds: if > 0, stop after this many tournament rounds in total (a
+ *               bounded sample of the work, for timing; the result is then not
+ *               converged).
+ *   sweeps_out: number of sweeps run; off_out: max |gamma|/sqrt(alpha beta) over
+ *               all pairs at exit.
+ * Returns 0 when converged, 1 when a limit was hit, -1 on bad arguments.
  */
 int oracle_jacobi_svd(int64_t m, int64_t n, const double *A, double *sigma, double *U,
-                      double *V, double eps, int max_sweeps, int nthreads,
+                      double *V, double eps, int max_sweeps, int max_rounds, int nthreads,
                       int *sweeps_out, double *off_out)
 {
     if (m < n || n <= 0 || !A || !sigma || !U || !V)
@@ -107,8 +110,9 @@ int oracle_jacobi_svd(int64_t m, int64_t n, const double *A, double *sigma, doub
     for (int64_t c = 0; c < n; ++c)
         Vc[c * n + c] = 1.0;
 
-    int sweeps = 0, converged = 0;
-    while (sweeps < max_sweeps && !converged) {
+    int sweeps = 0, converged = 0, limited = 0;
+    int64_t rounds_done = 0;
+    while (sweeps < max_sweeps && !converged && !limited) {
         ++sweeps;
         int rotations = 0;
         for (int64_t i = 0; i < np2; ++i)
@@ -130,8 +134,12 @@ int oracle_jacobi_svd(int64_t m, int64_t n, const double *A, double *sigma, doub
             for (int64_t i = np2 - 1; i > 1; --i)
                 ring[i] = ring[i - 1];
             ring[1] = last;
+            if (max_rounds > 0 && ++rounds_done >= max_rounds) {
+                limited = 1;
+                break;
+            }
         }
-        if (rotations == 0)
+        if (rotations == 0 && !limited)
             converged = 1;
     }
 

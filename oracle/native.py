@@ -41,7 +41,7 @@ def _load():
             dp = ctypes.POINTER(ctypes.c_double)
             lib.oracle_jacobi_svd.argtypes = [
                 ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp, ctypes.c_double,
-                ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]
             lib.oracle_jacobi_svd.restype = ctypes.c_int
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -54,7 +54,7 @@ def num_threads() -> int:
 
 
 def jacobi_svd(a: np.ndarray, eps: float = 0.0, max_sweeps: int = 60, nthreads: int = 0,
-               return_info: bool = False):
+               return_info: bool = False, max_rounds: int = 0):
     """Thin SVD ``a = U diag(sigma) V^T`` of a real matrix by one-sided Jacobi in FP64.
 
     Works on ``a`` when m >= n and on ``a.T`` otherwise (then U and V swap), so U
@@ -75,7 +75,7 @@ def jacobi_svd(a: np.ndarray, eps: float = 0.0, max_sweeps: int = 60, nthreads: 
     dp = ctypes.POINTER(ctypes.c_double)
     rc = _load().oracle_jacobi_svd(
         mm, nn, w.ctypes.data_as(dp), sigma.ctypes.data_as(dp), u.ctypes.data_as(dp),
-        v.ctypes.data_as(dp), float(eps), int(max_sweeps), int(nthreads),
+        v.ctypes.data_as(dp), float(eps), int(max_sweeps), int(max_rounds), int(nthreads),
         ctypes.byref(sweeps), ctypes.byref(off))
     if rc < 0:
         raise ValueError("oracle_jacobi_svd: bad arguments")

@@ -1,0 +1,268 @@
+"""ctypes binding of libsvt (include/svt.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module turns
+torch tensors into device pointers and the current torch stream into a
+cudaStream_t, and raises on error statuses. PyTorch is used only for device
+memory (the workspace, outputs) and streams. If libsvt.so is missing the import
+fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsvt.so")
+
+# svt_status
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_DIVERGED, ERR_TIMEOUT, \
+    ERR_NOT_READY, ERR_BUSY, ERR_UNSUPPORTED = range(10)
+# svt_precision
+FP64, FP32, BF16 = 0, 1, 2
+PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
+# svt_schedule_kind / svt_norm_kind / svt_mode
+SCHED_AUTO, SCHED_PE5, SCHED_NS3 = 0, 1, 2
+SCHED = {"auto": SCHED_AUTO, "pe5": SCHED_PE5, "ns3": SCHED_NS3}
+NORM_AUTO, NORM_FRO, NORM_GRAM = 0, 1, 2
+NORM = {"auto": NORM_AUTO, "fro": NORM_FRO, "gram": NORM_GRAM}
+MODE_SVT, MODE_RANK_R = 0, 1
+MODE = {"svt": MODE_SVT, "rank_r": MODE_RANK_R}
+
+# Every symbol include/svt.h declares.
+EXPORTS = [
+    "svt_status_str", "svt_options_default", "svt_workspace_bytes_ex", "svt_workspace_bytes",
+    "svt_ctx_create", "svt_ctx_destroy", "svt_polar", "svt_polar_ex", "svt_batch",
+    "svt_batch_workspace_bytes", "svt_serve_submit", "svt_serve_poll", "svt_serve_release",
+    "svt_ctx_sync", "svt_schedule_coeffs", "svt_debug_gemm_bf16", "svt_ctx_launch_count",
+    "svt_ctx_profile", "svt_ctx_profile_read",
+]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("prec", ctypes.c_int), ("schedule", ctypes.c_int),
+                ("norm", ctypes.c_int), ("ell0", ctypes.c_double), ("delta", ctypes.c_double),
+                ("polish", ctypes.c_int), ("mode", ctypes.c_int)]
+
+
+class Matrix(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("tau", ctypes.c_float), ("Y", ctypes.c_void_p),
+                ("ldy", ctypes.c_int64), ("opt", Options), ("d_status", ctypes.c_void_p)]
+
+
+class SVTError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_str(status)}")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libsvt.so (built by ``build.build()``); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libsvt.so not built at {LIB_PATH}: run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        L.svt_status_str.argtypes = [i32]
+        L.svt_status_str.restype = ctypes.c_char_p
+        L.svt_options_default.argtypes = [ctypes.POINTER(Options)]
+        L.svt_options_default.restype = None
+        L.svt_workspace_bytes_ex.argtypes = [i64, i64, ctypes.POINTER(Options),
+                                             ctypes.POINTER(ctypes.c_size_t)]
+        L.svt_workspace_bytes.argtypes = [i64, i64, i32, ctypes.POINTER(ctypes.c_size_t)]
+        L.svt_ctx_create.argtypes = [i32, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+        L.svt_ctx_destroy.argtypes = [vp]
+        L.svt_polar.argtypes = [vp, vp, i64, i64, i64, ctypes.c_float, i32, i32, vp, i64, vp, vp]
+        L.svt_polar_ex.argtypes = [vp, vp, i64, i64, i64, ctypes.c_float, ctypes.POINTER(Options),
+                                   vp, i64, vp, vp]
+        L.svt_batch.argtypes = [vp, ctypes.POINTER(Matrix), i32, vp]
+        L.svt_batch_workspace_bytes.argtypes = [ctypes.POINTER(Matrix), i32,
+                                                ctypes.POINTER(ctypes.c_size_t)]
+        L.svt_serve_submit.argtypes = [vp, ctypes.POINTER(Matrix), ctypes.POINTER(ctypes.c_uint64)]
+        L.svt_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
+        L.svt_serve_release.argtypes = [vp, ctypes.c_uint64]
+        L.svt_ctx_sync.argtypes = [vp, vp]
+        L.svt_schedule_coeffs.argtypes = [i32, i32, ctypes.c_double, ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_double)]
+        L.svt_debug_gemm_bf16.argtypes = [vp, i32, vp, vp, vp, vp, i64, i64, i64, i64, i64, vp,
+                                          i64, i32, vp]
+        L.svt_ctx_launch_count.argtypes = [vp]
+        L.svt_ctx_launch_count.restype = ctypes.c_uint64
+        L.svt_ctx_profile.argtypes = [vp, i32]
+        L.svt_ctx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_uint64)]
+        for name in EXPORTS:
+            if name not in ("svt_status_str", "svt_options_default", "svt_ctx_launch_count"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def status_str(s: int) -> str:
+    return lib().svt_status_str(int(s)).decode()
+
+
+def _check(st: int, where: str):
+    if st != OK:
+        raise SVTError(st, where)
+
+
+def make_options(iters: int = 20, prec="bf16", schedule="auto", norm="auto", ell0: float = 1e-3,
+                 delta: float = -1.0, polish: bool = True, mode="svt") -> Options:
+    o = Options()
+    lib().svt_options_default(ctypes.byref(o))
+    o.iters = int(iters)
+    o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    o.schedule = SCHED[schedule] if isinstance(schedule, str) else int(schedule)
+    o.norm = NORM[norm] if isinstance(norm, str) else int(norm)
+    o.ell0 = float(ell0)
+    o.delta = float(delta)
+    o.polish = 1 if polish else 0
+    o.mode = MODE[mode] if isinstance(mode, str) else int(mode)
+    return o
+
+
+def workspace_bytes(m: int, n: int, **opts) -> int:
+    out = ctypes.c_size_t(0)
+    o = make_options(**opts)
+    _check(lib().svt_workspace_bytes_ex(int(m), int(n), ctypes.byref(o), ctypes.byref(out)),
+           "svt_workspace_bytes_ex")
+    return int(out.value)
+
+
+def schedule_coeffs(kind="pe5", iters: int = 20, ell0: float = 1e-3, delta: float = 0.0) -> np.ndarray:
+    """The library's own polynomial schedule, (iters, 3) array of (a, b, c)."""
+    buf = (ctypes.c_double * max(1, 3 * iters))()
+    k = SCHED[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().svt_schedule_coeffs(k, int(iters), float(ell0), float(delta), buf),
+           "svt_schedule_coeffs")
+    return np.array(buf[: 3 * iters], dtype=np.float64).reshape(iters, 3)
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def _f32_matrix(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D tensor")
+    if t.dtype != torch.float32 or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA float32 tensor")
+    if t.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major (unit column stride)")
+    return t.data_ptr(), t.size(0), t.size(1), t.stride(0)
+
+
+class Context:
+    """A libsvt context with a torch-allocated device workspace."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 1 << 28):
+        import torch
+        self.device = int(device)
+        self.workspace = torch.empty(max(256, int(workspace_bytes)), dtype=torch.uint8,
+                                     device=f"cuda:{self.device}")
+        h = ctypes.c_void_p()
+        _check(lib().svt_ctx_create(self.device, ctypes.c_void_p(self.workspace.data_ptr()),
+                                    self.workspace.numel(), ctypes.byref(h)), "svt_ctx_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().svt_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ensure_workspace(self, nbytes: int):
+        """Grow the workspace (re-creating the context) if it is smaller than nbytes."""
+        import torch
+        if nbytes <= self.workspace.numel():
+            return
+        torch.cuda.synchronize(self.device)
+        self.close()
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=f"cuda:{self.device}")
+        h = ctypes.c_void_p()
+        _check(lib().svt_ctx_create(self.device, ctypes.c_void_p(self.workspace.data_ptr()),
+                                    self.workspace.numel(), ctypes.byref(h)), "svt_ctx_create")
+        self.handle = h
+
+    def polar(self, A, tau: float, out=None, status=None, stream=None, **opts):
+        """Y = A_tau through svt_polar_ex (asynchronous on the current stream)."""
+        import torch
+        a_ptr, m, n, lda = _f32_matrix(A, "A")
+        if out is None:
+            out = torch.empty((m, n), dtype=torch.float32, device=A.device)
+        y_ptr, ym, yn, ldy = _f32_matrix(out, "out")
+        if (ym, yn) != (m, n):
+            raise ValueError("out has the wrong shape")
+        o = make_options(**opts)
+        self.ensure_workspace(workspace_bytes(m, n, **opts))
+        st_ptr = status.data_ptr() if status is not None else None
+        _check(lib().svt_polar_ex(self.handle, ctypes.c_void_p(a_ptr), m, n, lda,
+                                  ctypes.c_float(tau), ctypes.byref(o), ctypes.c_void_p(y_ptr),
+                                  ldy, ctypes.c_void_p(st_ptr), ctypes.c_void_p(_stream_ptr(stream))),
+               "svt_polar_ex")
+        return out
+
+    def polar_basic(self, A, tau: float, iters: int, prec="bf16", out=None, status=None,
+                    stream=None):
+        """The svt_polar entry point (default options apart from iters and precision)."""
+        import torch
+        a_ptr, m, n, lda = _f32_matrix(A, "A")
+        if out is None:
+            out = torch.empty((m, n), dtype=torch.float32, device=A.device)
+        y_ptr, _, _, ldy = _f32_matrix(out, "out")
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        self.ensure_workspace(workspace_bytes(m, n, prec=p))
+        st_ptr = status.data_ptr() if status is not None else None
+        _check(lib().svt_polar(self.handle, ctypes.c_void_p(a_ptr), m, n, lda, ctypes.c_float(tau),
+                               int(iters), p, ctypes.c_void_p(y_ptr), ldy, ctypes.c_void_p(st_ptr),
+                               ctypes.c_void_p(_stream_ptr(stream))), "svt_polar")
+        return out
+
+    def debug_gemm_bf16(self, nseg, L_hi, L_lo, R_hi, R_lo, D, sym=False, stream=None):
+        """D = sum of segment products (see svt_debug_gemm_bf16)."""
+        M, K = L_hi.shape
+        N = R_hi.shape[0]
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else None)
+        _check(lib().svt_debug_gemm_bf16(self.handle, int(nseg), ptr(L_hi), ptr(L_lo), ptr(R_hi),
+                                         ptr(R_lo), M, N, K, L_hi.stride(0), R_hi.stride(0),
+                                         ptr(D), D.stride(0), 1 if sym else 0,
+                                         ctypes.c_void_p(_stream_ptr(stream))),
+               "svt_debug_gemm_bf16")
+        return D
+
+    def sync(self, stream=None):
+        _check(lib().svt_ctx_sync(self.handle, ctypes.c_void_p(_stream_ptr(stream))), "svt_ctx_sync")
+
+    def launch_count(self) -> int:
+        return int(lib().svt_ctx_launch_count(self.handle))
+
+    def profile(self, enable: bool = True):
+        _check(lib().svt_ctx_profile(self.handle, 1 if enable else 0), "svt_ctx_profile")
+
+    def profile_read(self):
+        """(device ms, algorithmic flops, launches) of the tensor-core launches since the last reset."""
+        ms, fl, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+        _check(lib().svt_ctx_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(fl),
+                                          ctypes.byref(n)), "svt_ctx_profile_read")
+        return ms.value, fl.value, int(n.value)

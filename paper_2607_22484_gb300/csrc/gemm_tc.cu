@@ -1,0 +1,622 @@
+// Tensor-core product kernel for sm_103a: D = sum_s L_s R_s^T with BF16
+// operands staged by TMA into 128-byte-swizzled shared memory, tcgen05.mma
+// (kind::f16, BF16 x BF16 -> FP32) accumulating in tensor memory, and a fused
+// epilogue that reads the accumulator back with tcgen05.ld.
+//
+// This one kernel carries every dense product of the method (Section 2): the
+// shifted Gram A^T A - tau^2 I, the polynomial steps X (a I + b X^T X +
+// c (X^T X)^2) of both polar chains, the polish step and the final combine
+// 1/2 (A - tau P)(I + S) of Proposition 1.
+//
+// Structure (persistent, one CTA per SM, 192 threads):
+//   warp 0    : TMA producer (one thread), STAGES-deep shared-memory ring.
+//   warp 1    : tensor-memory allocator and MMA issuer (one thread).
+//   warps 2-5 : epilogue; warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31.
+// Two accumulator buffers of BN FP32 columns each let the epilogue of one tile
+// overlap the MMAs of the next.
+//
+// Every wait on an mbarrier is bounded (kWaitTimeoutNs of global time); on
+// expiry the kernel records SVT_ERR_TIMEOUT in the problem's status word, the
+// other roles stop at their next wait, in-flight copies and MMAs are drained
+// (again with a bound) and tensor memory is released before the kernel returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "svt_internal.h"
+
+namespace svt {
+
+namespace {
+
+constexpr uint64_t kWaitTimeoutNs = 2000000000ull;  // 2 s
+constexpr int kThreads = 192;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete. Returns false
+// when the kernel is aborting (another role timed out) or this wait timed out.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                          int *status, uint64_t limit_ns)
+{
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if ((it & 255u) == 255u) {
+            if (*abort_flag)
+                return false;
+            uint64_t now = global_timer_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > limit_ns) {
+                *abort_flag = 1;
+                if (status)
+                    atomicCAS(status, 0, (int)SVT_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand tile laid out by TMA
+// with 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)(16u >> 4) << 16;          // leading byte offset (unused here)
+    d |= (uint64_t)(1024u >> 4) << 32;        // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n)
+{
+    return (1u << 4)                       // D format FP32
+           | (1u << 7)                     // A format BF16
+           | (1u << 10)                    // B format BF16
+           | ((uint32_t)(n >> 3) << 17)    // N / 8
+           | ((uint32_t)(m >> 4) << 24);   // M / 16
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 32 consecutive FP32 columns of tensor memory into registers.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------- tiles
+
+struct TileCoord {
+    int prob, tm, tn;
+    bool valid;
+};
+
+// Linear tile index -> (problem, tile row, tile column).
+// Dense problems: column-major over the tile grid. Symmetric problems: only
+// tiles holding some element with row <= col; column tn holds r (tn + 1) row
+// tiles (r = BN / BM), so the first tile of column tn is r tn (tn + 1) / 2.
+template <int BN>
+__device__ TileCoord decode_tile(const TcLaunch &L, int t)
+{
+    TileCoord tc{0, 0, 0, false};
+    int p = 0;
+    while (p + 1 < L.nprob && t >= L.tile_start[p + 1])
+        ++p;
+    const TcProblem &P = L.p[p];
+    int local = t - L.tile_start[p];
+    tc.prob = p;
+    if (!P.sym) {
+        tc.tm = local % P.tiles_m;
+        tc.tn = local / P.tiles_m;
+        tc.valid = true;
+        return tc;
+    }
+    constexpr int r = BN / kBM;
+    int tn = (int)((sqrtf(8.0f * (float)local / (float)r + 1.0f) - 1.0f) * 0.5f);
+    while (tn > 0 && r * tn * (tn + 1) / 2 > local)
+        --tn;
+    while (r * (tn + 1) * (tn + 2) / 2 <= local)
+        ++tn;
+    int tm = local - r * tn * (tn + 1) / 2;
+    tc.tm = tm;
+    tc.tn = tn;
+    tc.valid = (tm < P.tiles_m) && (tn < P.tiles_n);
+    return tc;
+}
+
+// ------------------------------------------------------------- epilogue
+
+struct EpiScales {
+    float alpha, beta, gamma;
+};
+
+__device__ __forceinline__ EpiScales epi_scales(const Epi &e)
+{
+    EpiScales s{(float)e.alpha, (float)e.beta, (float)e.gamma};
+    if (e.theta_src) {
+        double theta = pow(*e.theta_src, e.theta_pow);
+        if (theta > 0.0 && isfinite(theta)) {
+            s.alpha = (float)(e.alpha * pow(theta, -e.ea));
+            s.beta = (float)(e.beta * pow(theta, -e.eb));
+            s.gamma = (float)(e.gamma * pow(theta, -e.eg));
+        } else if (e.status) {
+            atomicCAS(e.status, 0, (int)SVT_ERR_DIVERGED);
+        }
+    }
+    return s;
+}
+
+__device__ __forceinline__ float load_c(const Epi &e, int64_t r, int64_t c)
+{
+    int64_t off = e.c_trans ? c * e.ldc + r : r * e.ldc + c;
+    switch (e.c_kind) {
+    case C_BF16:
+        return __bfloat162float(static_cast<const __nv_bfloat16 *>(e.c0)[off]);
+    case C_PAIR:
+        return __bfloat162float(static_cast<const __nv_bfloat16 *>(e.c0)[off]) +
+               __bfloat162float(static_cast<const __nv_bfloat16 *>(e.c1)[off]);
+    case C_F32:
+        return static_cast<const float *>(e.c0)[off];
+    default:
+        return 0.0f;
+    }
+}
+
+__device__ __forceinline__ void store_val(int kind, void *p0, void *p1, int64_t off, float v)
+{
+    if (kind == O_BF16) {
+        static_cast<__nv_bfloat16 *>(p0)[off] = __float2bfloat16_rn(v);
+    } else if (kind == O_PAIR) {
+        __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        static_cast<__nv_bfloat16 *>(p0)[off] = hi;
+        static_cast<__nv_bfloat16 *>(p1)[off] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    } else if (kind == O_F32) {
+        static_cast<float *>(p0)[off] = v;
+    }
+}
+
+// Row-major store of 32 consecutive values of one row, vectorised when the
+// whole chunk is in range and 16-byte aligned.
+__device__ __forceinline__ void store_row32(int kind, void *p0, void *p1, int64_t ld, int64_t r,
+                                            int64_t c0, const float *v, int ncol_valid,
+                                            uint32_t mask)
+{
+    int64_t off = r * ld + c0;
+    bool full = (ncol_valid == 32) && (mask == 0xffffffffu);
+    if (full && (kind == O_BF16 || kind == O_PAIR) && ((off & 7) == 0)) {
+        uint4 *dh = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(p0) + off);
+        uint4 *dl = (kind == O_PAIR)
+                        ? reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(p1) + off)
+                        : nullptr;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            __align__(16) __nv_bfloat16 hi[8];
+            __align__(16) __nv_bfloat16 lo[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                hi[i] = __float2bfloat16_rn(v[q * 8 + i]);
+                lo[i] = __float2bfloat16_rn(v[q * 8 + i] - __bfloat162float(hi[i]));
+            }
+            dh[q] = *reinterpret_cast<uint4 *>(hi);
+            if (dl)
+                dl[q] = *reinterpret_cast<uint4 *>(lo);
+        }
+        return;
+    }
+    if (full && kind == O_F32 && ((off & 3) == 0)) {
+        float4 *d = reinterpret_cast<float4 *>(static_cast<float *>(p0) + off);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        if (i < ncol_valid && ((mask >> i) & 1u))
+            store_val(kind, p0, p1, off + i, v[i]);
+}
+
+// Apply the epilogue to the 32 accumulators of row r, columns c0 .. c0 + 31.
+__device__ __forceinline__ void epilogue_chunk(const TcProblem &P, const EpiScales &s, int64_t r,
+                                               int64_t c0, float *v, double &nrm)
+{
+    const Epi &e = P.ep;
+    const bool row_ok = r < P.M;
+    const int64_t rem = (int64_t)P.N - c0;
+    int ncol = rem < 32 ? (int)rem : 32;
+    if (ncol < 0)
+        ncol = 0;
+    uint32_t mask = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        int64_t c = c0 + i;
+        float x = s.alpha * v[i];
+        bool ok = row_ok && i < ncol && (!P.sym || r <= c);
+        if (ok) {
+            if (e.c_kind != C_NONE)
+                x += s.beta * load_c(e, r, c);
+            if (r == c) {
+                x += s.gamma;
+                if (e.diag)
+                    x = (float)(e.diag[r] * e.dss[0] - e.dss[1]);
+            }
+            mask |= (1u << i);
+            if (e.norm_acc) {
+                double xd = (double)x;
+                nrm += (P.sym && r != c) ? 2.0 * xd * xd : xd * xd;
+            }
+        }
+        v[i] = x;
+    }
+    if (!row_ok)
+        return;
+    // Main output.
+    if (e.o_trans) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if ((mask >> i) & 1u)
+                store_val(e.o_kind, e.o0, e.o1, (c0 + i) * e.ldo + r, v[i]);
+    } else {
+        store_row32(e.o_kind, e.o0, e.o1, e.ldo, r, c0, v, ncol, mask);
+    }
+    // Mirror of a symmetric result: (c, r) for r < c.
+    if (P.sym) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (((mask >> i) & 1u) && (c0 + i) != r)
+                store_val(e.o_kind, e.o0, e.o1, (c0 + i) * e.ldo + r, v[i]);
+    }
+    // Extra transposed copy (X^T next to X).
+    if (e.t_kind != O_NONE) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if ((mask >> i) & 1u)
+                store_val(e.t_kind, e.t0, e.t1, (c0 + i) * e.ldt + r, v[i]);
+    }
+}
+
+// --------------------------------------------------------------- kernel
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcLaunch L)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                ~static_cast<uintptr_t>(1023));
+    constexpr int A_BYTES = kBM * kBK * 2;
+    constexpr int B_BYTES = BN * kBK * 2;
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + STAGES * A_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + STAGES * B_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *drain = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    int *skip_flag = reinterpret_cast<int *>(tmem_slot + 2);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    int *status0 = L.p[0].ep.status;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 128);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        // A solve whose earlier launch already timed out does no further work.
+        *skip_flag = (status0 && *reinterpret_cast<volatile int *>(status0) == (int)SVT_ERR_TIMEOUT);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(2 * BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int total = *skip_flag ? 0 : L.tile_start[L.nprob];
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------ TMA producer
+        int stage = 0;
+        uint32_t phase = 0;
+        bool issued[STAGES];
+        uint32_t issued_parity[STAGES];
+        for (int s = 0; s < STAGES; ++s) {
+            issued[s] = false;
+            issued_parity[s] = 0;
+        }
+        bool ok = true;
+        for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            TileCoord tc = decode_tile<BN>(L, t);
+            if (!tc.valid)
+                continue;
+            const TcProblem &P = L.p[tc.prob];
+            const int kblocks = (P.K + kBK - 1) / kBK;
+            for (int sg = 0; sg < P.nseg && ok; ++sg) {
+                const CUtensorMap *mL = &P.mapL[P.segL[sg]];
+                const CUtensorMap *mR = &P.mapR[P.segR[sg]];
+                for (int kb = 0; kb < kblocks; ++kb) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, status0, kWaitTimeoutNs)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[stage], (uint32_t)(A_BYTES + B_BYTES));
+                    tma_load_2d(sA + stage * A_BYTES, mL, kb * kBK, tc.tm * kBM, &full[stage]);
+                    tma_load_2d(sB + stage * B_BYTES, mR, kb * kBK, tc.tn * BN, &full[stage]);
+                    issued[stage] = true;
+                    issued_parity[stage] = phase;
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+        }
+        // Drain: the last copy into every stage must have landed before exit.
+        for (int s = 0; s < STAGES; ++s)
+            if (issued[s]) {
+                volatile int no_abort = 0;
+                mbar_wait(&full[s], issued_parity[s], &no_abort, nullptr, kWaitTimeoutNs / 4);
+            }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------ MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+        int stage = 0;
+        uint32_t phase = 0;
+        int buf = 0;
+        uint32_t tphase = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            TileCoord tc = decode_tile<BN>(L, t);
+            if (!tc.valid)
+                continue;
+            const TcProblem &P = L.p[tc.prob];
+            const int kblocks = (P.K + kBK - 1) / kBK;
+            if (!mbar_wait(&tempty[buf], tphase ^ 1u, abort_flag, status0, kWaitTimeoutNs))
+                break;
+            tc_fence_after();
+            const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+            uint32_t acc = 0;
+            for (int sg = 0; sg < P.nseg && ok; ++sg) {
+                for (int kb = 0; kb < kblocks; ++kb) {
+                    if (!mbar_wait(&full[stage], phase, abort_flag, status0, kWaitTimeoutNs)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + stage * A_BYTES);
+                    const uint32_t b0 = smem_u32(sB + stage * B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        mma_bf16(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                                 acc);
+                        acc = 1;
+                    }
+                    mma_commit(&empty[stage]);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok)
+                break;
+            mma_commit(&tfull[buf]);
+            if (++buf == 2) {
+                buf = 0;
+                tphase ^= 1u;
+            }
+        }
+        // Drain: every MMA issued so far completes before tensor memory is freed.
+        mma_commit(drain);
+        volatile int no_abort = 0;
+        mbar_wait(drain, 0, &no_abort, nullptr, kWaitTimeoutNs / 4);
+    } else if (warp >= 2) {
+        // ------------------------------------------------ epilogue
+        const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+        const int row_in_tile = quad * 32 + lane;
+        int buf = 0;
+        uint32_t tphase = 0;
+        int last_prob = -1;
+        EpiScales sc{1.f, 0.f, 0.f};
+        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+            TileCoord tc = decode_tile<BN>(L, t);
+            if (!tc.valid)
+                continue;
+            const TcProblem &P = L.p[tc.prob];
+            if (tc.prob != last_prob) {
+                sc = epi_scales(P.ep);
+                last_prob = tc.prob;
+            }
+            if (!mbar_wait(&tfull[buf], tphase, abort_flag, status0, kWaitTimeoutNs))
+                break;
+            tc_fence_after();
+            const int64_t r = (int64_t)tc.tm * kBM + row_in_tile;
+            const int64_t warp_row0 = (int64_t)tc.tm * kBM + quad * 32;
+            double nrm = 0.0;
+#pragma unroll 1
+            for (int ch = 0; ch < BN / 32; ++ch) {
+                const int64_t c0 = (int64_t)tc.tn * BN + ch * 32;
+                // Warp-uniform skips: chunk right of N, or wholly below the diagonal.
+                if (c0 >= P.N || warp_row0 >= P.M)
+                    continue;
+                if (P.sym && warp_row0 > c0 + 31)
+                    continue;
+                float v[32];
+                tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + ch * 32), v);
+                epilogue_chunk(P, sc, r, c0, v, nrm);
+            }
+            if (P.ep.norm_acc) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+                if (lane == 0 && nrm != 0.0)
+                    atomicAdd(P.ep.norm_acc, nrm);
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty[buf]);
+            if (++buf == 2) {
+                buf = 0;
+                tphase ^= 1u;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(2 * BN));
+    }
+}
+
+template <int BN, int STAGES>
+constexpr int smem_bytes()
+{
+    return STAGES * (kBM + BN) * kBK * 2 + 1024 /* alignment slack */ + 256 /* barriers */;
+}
+
+template <int BN, int STAGES>
+cudaError_t launch_bn(const TcLaunch &l, int num_sms, cudaStream_t s)
+{
+    static bool configured = false;
+    constexpr int smem = smem_bytes<BN, STAGES>();
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess)
+            return e;
+        configured = true;
+    }
+    int total = l.tile_start[l.nprob];
+    if (total <= 0)
+        return cudaSuccess;
+    int grid = total < num_sms ? total : num_sms;
+    tc_gemm_kernel<BN, STAGES><<<grid, kThreads, smem, s>>>(l);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+int tc_num_tiles(const TcProblem &p, int bn)
+{
+    if (!p.sym)
+        return p.tiles_m * p.tiles_n;
+    int r = bn / kBM;
+    return r * p.tiles_n * (p.tiles_n + 1) / 2;
+}
+
+cudaError_t tc_gemm_launch(const TcLaunch &l, int bn, int num_sms, cudaStream_t s)
+{
+    if (bn == 256)
+        return launch_bn<256, 4>(l, num_sms, s);
+    if (bn == 128)
+        return launch_bn<128, 6>(l, num_sms, s);
+    return cudaErrorInvalidValue;
+}
+
+} // namespace svt

@@ -1,0 +1,145 @@
+// Host-side plan structures of libsvt, shared by svt_api.cu and serve.cpp.
+//
+// A plan is the launch sequence of one solve for a fixed shape, option set and
+// workspace offset: the tensor maps and static epilogue parameters are built
+// once; per call only the input/output pointers and tau are patched in.
+#pragma once
+
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "svt_internal.h"
+
+namespace svt {
+
+constexpr int64_t kF64MaxDim = 4096;
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+inline int64_t ld_of(int64_t cols) { return (cols + 63) / 64 * 64; }
+
+// Options with defaults applied.
+struct Resolved {
+    int iters;
+    int prec;
+    int schedule;   // SVT_SCHED_PE5 or SVT_SCHED_NS3
+    int norm;       // SVT_NORM_FRO or SVT_NORM_GRAM
+    double ell0, delta;
+    int polish;
+    int mode;
+};
+
+bool resolve(const svt_options *in, Resolved *r);
+
+// A matrix buffer in the workspace: hi part and (FP32-class pairs) lo part.
+struct Buf {
+    size_t hi = 0, lo = 0;   // byte offsets (lo == 0: absent)
+    int64_t rows = 0, cols = 0, ld = 0;
+    bool has_lo = false;
+};
+
+struct Layout {
+    int64_t M = 0, N = 0, ldM = 0, ldN = 0;
+    size_t esz = 2;          // element size of matrix buffers (2 BF16, 8 FP64)
+    size_t scal = 0, status = 0, colnorm = 0;
+    Buf X[2], Xt[2], XtLo0, S[2], Yp, Zp, Ys, Zs, ZPp, ZSp, B, Sp;
+    size_t total = 0;
+};
+
+Layout make_layout(int64_t m, int64_t n, const Resolved &r);
+
+// ------------------------------------------------------------ plan
+
+enum OpKind { OP_MEMSET, OP_REDUCE, OP_SPLIT, OP_TC, OP_F64, OP_PREP, OP_FINAL };
+enum Patch { PT_C_IS_A = 1, PT_O_IS_Y = 2, PT_ALPHA_NEG_TAU = 4 };
+
+struct Op {
+    int kind;
+    int idx;      // index into tc / f64 arrays
+    int bn;       // TC tile width
+};
+
+struct PatchRec {
+    int kind;     // OP_TC / OP_F64
+    int launch, prob, flags;
+};
+
+struct Plan {
+    int64_t m, n;
+    bool wide;
+    Resolved opt;
+    Layout lay;
+    size_t ws_base;
+    std::vector<double> coef;
+    std::vector<Op> ops;
+    std::vector<TcLaunch> tc;
+    std::vector<F64Launch> f64;
+    std::vector<PatchRec> patches;
+    std::vector<double> tc_flops;   // algorithmic flops of each tensor-core launch
+    int tc_launches_per_solve = 0;
+    int kernel_launches = 0;
+};
+
+struct Key {
+    int64_t m, n;
+    int iters, prec, schedule, norm, polish, mode;
+    double ell0, delta;
+    size_t ws_base;
+    bool operator<(const Key &o) const
+    {
+        return std::tie(m, n, iters, prec, schedule, norm, polish, mode, ell0, delta, ws_base) <
+               std::tie(o.m, o.n, o.iters, o.prec, o.schedule, o.norm, o.polish, o.mode, o.ell0,
+                        o.delta, o.ws_base);
+    }
+};
+
+
+struct CallArgs {
+    const float *A;
+    int64_t lda;
+    float tau;
+    float *Y;
+    int64_t ldy;
+    svt_status *d_status;
+};
+
+svt_status validate(const float *A, int64_t m, int64_t n, int64_t lda, float tau, const float *Y,
+                    int64_t ldy);
+
+} // namespace svt
+
+// Serving state of a context (serve.cpp).
+struct ServeState;
+
+struct svt_ctx {
+    int device = 0;
+    int num_sms = 0;
+    uint8_t *ws = nullptr;
+    size_t ws_bytes = 0;
+    uint64_t launches = 0;
+    std::map<svt::Key, std::unique_ptr<svt::Plan>> plans;
+    std::mutex mu;
+    ServeState *serve = nullptr;
+    // Optional per-launch timing of the tensor-core kernel (svt_ctx_profile).
+    bool profile = false;
+    std::vector<cudaEvent_t> prof_pool;
+    struct ProfRec { cudaEvent_t a, b; double flops; };
+    std::vector<ProfRec> prof_pending;
+    size_t prof_next = 0;
+};
+
+namespace svt {
+svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_t ws_base,
+                    size_t ws_avail, Plan **out);
+svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s);
+// Read the plan's internal status word back to host memory (async on s).
+svt_status plan_status_copy(svt_ctx *ctx, const Plan &P, int *host_dst, cudaStream_t s);
+void serve_shutdown(svt_ctx *ctx);
+bool serve_busy(svt_ctx *ctx);
+} // namespace svt

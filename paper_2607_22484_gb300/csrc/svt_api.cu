@@ -1,0 +1,995 @@
+// libsvt host side: context, workspace layout, launch plans and the solve
+// sequence of Proposition 1 in the factored form A_tau = 1/2 (A - tau P)(I + S).
+//
+// One solve of an m x n matrix works on the tall orientation (M, N) =
+// (max(m, n), min(m, n)); the wide case (n > m) is the footnote's A A^T branch,
+// i.e. the tall problem of A^T, with the result written transposed.
+//
+//   ingest   : FP64 ||A||_F^2 and Gram diagonal; X0 = A / alpha (alpha a power
+//              of two) as BF16 (or FP64) in both orientations.
+//   Gram     : S0 = (A^T A - tau^2 I) / alpha^2, FP32-class product (three
+//              BF16 products of hi/lo parts), diagonal recomputed in FP64 with
+//              the tau^2 shift (Section 4 shifts by tau**2), ||S0||_F^2 in FP64.
+//   chains   : per step t, for P (X: M x N) and S (symmetric N x N) together:
+//                Y = X^T X;  Z = c_t Y^2 + b_t Y + a_t I;  X <- X Z,
+//              the first step scaled by the chain's norm bound theta.
+//   polish   : one cubic Newton-Schulz step per chain in the FP32-class tier;
+//              the P polish writes B = A - tau P directly.
+//   combine  : Y = 1/2 (B S + B) in the FP32-class tier, stored as FP32.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "plan.h"
+
+namespace svt {
+
+// ------------------------------------------------------------ tensor maps
+
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+std::once_flag g_encode_once;
+
+void resolve_encode()
+{
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+}
+} // namespace
+
+bool encode_bf16_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld,
+                     int box_rows)
+{
+    std::call_once(g_encode_once, resolve_encode);
+    if (!g_encode || !ptr || rows <= 0 || cols <= 0 || (ld % 8) != 0 ||
+        (reinterpret_cast<uintptr_t>(ptr) & 15) != 0)
+        return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+
+bool resolve(const svt_options *in, Resolved *r)
+{
+    svt_options o;
+    if (in)
+        o = *in;
+    else
+        svt_options_default(&o);
+    if (o.iters < 0 || o.iters > 1000)
+        return false;
+    if (o.prec != SVT_FP64 && o.prec != SVT_FP32 && o.prec != SVT_BF16)
+        return false;
+    r->iters = o.iters;
+    r->prec = o.prec;
+    r->schedule = (o.schedule == SVT_SCHED_NS3) ? SVT_SCHED_NS3 : SVT_SCHED_PE5;
+    if (o.schedule != SVT_SCHED_AUTO && o.schedule != SVT_SCHED_PE5 && o.schedule != SVT_SCHED_NS3)
+        return false;
+    if (o.norm == SVT_NORM_AUTO)
+        r->norm = (r->schedule == SVT_SCHED_PE5) ? SVT_NORM_GRAM : SVT_NORM_FRO;
+    else if (o.norm == SVT_NORM_FRO || o.norm == SVT_NORM_GRAM)
+        r->norm = o.norm;
+    else
+        return false;
+    r->ell0 = (o.ell0 > 0.0) ? o.ell0 : 1e-3;
+    if (!(r->ell0 < 1.0))
+        return false;
+    if (o.delta < 0.0)
+        r->delta = (o.prec == SVT_BF16) ? 0.01 : (o.prec == SVT_FP32 ? 1e-4 : 0.0);
+    else
+        r->delta = o.delta;
+    r->polish = o.polish ? 1 : 0;
+    if (o.mode != SVT_MODE_SVT && o.mode != SVT_MODE_RANK_R)
+        return false;
+    r->mode = o.mode;
+    return true;
+}
+
+namespace {
+struct Alloc {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        size_t o = off;
+        off = align_up(off + bytes, kAlign);
+        return o;
+    }
+};
+
+} // namespace
+
+static Buf make_buf(Alloc &a, int64_t rows, int64_t cols, size_t esz, bool pair)
+{
+    Buf b;
+    b.rows = rows;
+    b.cols = cols;
+    b.ld = ld_of(cols);
+    size_t bytes = (size_t)rows * (size_t)b.ld * esz;
+    b.hi = a.take(bytes);
+    b.has_lo = pair;
+    if (pair)
+        b.lo = a.take(bytes);
+    return b;
+}
+
+Layout make_layout(int64_t m, int64_t n, const Resolved &r)
+{
+    Layout L;
+    L.M = std::max(m, n);
+    L.N = std::min(m, n);
+    L.ldM = ld_of(L.M);
+    L.ldN = ld_of(L.N);
+    const bool f64 = r.prec == SVT_FP64;
+    const bool fp32 = r.prec == SVT_FP32;
+    L.esz = f64 ? 8 : 2;
+    const bool skipP = r.mode == SVT_MODE_RANK_R;
+    Alloc a;
+    L.scal = a.take(SC_COUNT * sizeof(double));
+    L.status = a.take(sizeof(int) * 4);
+    L.colnorm = a.take((size_t)L.N * sizeof(double));
+    const bool pairs = fp32;  // iterates carried as hi/lo pairs
+    for (int i = 0; i < 2; ++i) {
+        if (!skipP || i == 0)
+            L.X[i] = make_buf(a, L.M, L.N, L.esz, pairs && !f64);
+        if (!skipP || i == 0)
+            L.Xt[i] = make_buf(a, L.N, L.M, L.esz, pairs && !f64);
+    }
+    if (!f64 && !pairs)
+        L.XtLo0 = make_buf(a, L.N, L.M, L.esz, false);
+    for (int i = 0; i < 2; ++i)
+        L.S[i] = make_buf(a, L.N, L.N, L.esz, pairs);
+    if (!skipP) {
+        L.Yp = make_buf(a, L.N, L.N, L.esz, pairs);
+        L.Zp = make_buf(a, L.N, L.N, L.esz, pairs);
+        L.ZPp = make_buf(a, L.N, L.N, L.esz, !f64);
+    }
+    L.Ys = make_buf(a, L.N, L.N, L.esz, pairs);
+    L.Zs = make_buf(a, L.N, L.N, L.esz, pairs);
+    L.ZSp = make_buf(a, L.N, L.N, L.esz, !f64);
+    L.B = make_buf(a, L.M, L.N, L.esz, !f64);
+    L.Sp = make_buf(a, L.N, L.N, L.esz, !f64);
+    L.total = a.off;
+    return L;
+}
+
+} // namespace svt
+
+namespace svt {
+namespace {
+
+// ---------------------------------------------------------- plan builder
+
+struct Builder {
+    svt_ctx *ctx;
+    Plan *plan;
+    uint8_t *base;       // workspace base for this plan
+    int bn_default;
+
+    void *ptr(size_t off) { return base + off; }
+    double *scal(int slot) { return reinterpret_cast<double *>(base + plan->lay.scal) + slot; }
+    int *status() { return reinterpret_cast<int *>(base + plan->lay.status); }
+
+    Epi epi0()
+    {
+        Epi e;
+        std::memset(&e, 0, sizeof(e));
+        e.alpha = 1.0;
+        e.status = status();
+        return e;
+    }
+
+    // Output description for a Buf: BF16, pair or FP64.
+    void set_out(Epi &e, const Buf &b, bool pair)
+    {
+        const bool f64 = plan->opt.prec == SVT_FP64;
+        e.o_kind = f64 ? O_F64 : (pair ? O_PAIR : O_BF16);
+        e.o0 = ptr(b.hi);
+        e.o1 = pair ? ptr(b.lo) : nullptr;
+        e.ldo = b.ld;
+    }
+    void set_t(Epi &e, const Buf &b, bool pair)
+    {
+        const bool f64 = plan->opt.prec == SVT_FP64;
+        e.t_kind = f64 ? O_F64 : (pair ? O_PAIR : O_BF16);
+        e.t0 = ptr(b.hi);
+        e.t1 = pair ? ptr(b.lo) : nullptr;
+        e.ldt = b.ld;
+    }
+    void set_c(Epi &e, const Buf &b, double beta)
+    {
+        const bool f64 = plan->opt.prec == SVT_FP64;
+        e.c_kind = f64 ? C_F64 : (b.has_lo ? C_PAIR : C_BF16);
+        e.c0 = ptr(b.hi);
+        e.c1 = b.has_lo ? ptr(b.lo) : nullptr;
+        e.ldc = b.ld;
+        e.beta = beta;
+    }
+
+    // One product D = L R^T over the segment pattern implied by the operands'
+    // hi/lo parts (1, 2 or 3 BF16 products).
+    bool tc_problem(TcProblem &p, const Buf &L, const Buf &R, int M, int N, int K, bool sym,
+                    const Epi &e, int bn)
+    {
+        std::memset(&p, 0, sizeof(p));
+        if (!encode_bf16_map(&p.mapL[0], ptr(L.hi), L.rows, L.cols, L.ld, kBM))
+            return false;
+        if (!encode_bf16_map(&p.mapR[0], ptr(R.hi), R.rows, R.cols, R.ld, bn))
+            return false;
+        if (L.has_lo && !encode_bf16_map(&p.mapL[1], ptr(L.lo), L.rows, L.cols, L.ld, kBM))
+            return false;
+        if (R.has_lo && !encode_bf16_map(&p.mapR[1], ptr(R.lo), R.rows, R.cols, R.ld, bn))
+            return false;
+        int ns = 0;
+        p.segL[ns] = 0; p.segR[ns] = 0; ++ns;
+        if (R.has_lo) { p.segL[ns] = 0; p.segR[ns] = 1; ++ns; }
+        if (L.has_lo) { p.segL[ns] = 1; p.segR[ns] = 0; ++ns; }
+        p.nseg = ns;
+        p.M = M;
+        p.N = N;
+        p.K = K;
+        p.sym = sym ? 1 : 0;
+        p.tiles_m = (M + kBM - 1) / kBM;
+        p.tiles_n = (N + bn - 1) / bn;
+        p.ep = e;
+        return true;
+    }
+
+    void f64_problem(F64Problem &p, const Buf &L, const Buf &R, int M, int N, int K, bool sym,
+                     const Epi &e)
+    {
+        std::memset(&p, 0, sizeof(p));
+        p.L = static_cast<const double *>(ptr(L.hi));
+        p.R = static_cast<const double *>(ptr(R.hi));
+        p.ldl = L.ld;
+        p.ldr = R.ld;
+        p.M = M;
+        p.N = N;
+        p.K = K;
+        p.sym = sym ? 1 : 0;
+        p.ep = e;
+    }
+
+    // Grouped launch of up to two products (P chain and S chain of one step).
+    struct Prod {
+        const Buf *L, *R;
+        int M, N, K;
+        bool sym;
+        Epi e;
+        int patch;
+    };
+
+    bool emit(const std::vector<Prod> &prods)
+    {
+        if (prods.empty())
+            return true;
+        if (plan->opt.prec == SVT_FP64) {
+            F64Launch l;
+            std::memset(&l, 0, sizeof(l));
+            l.nprob = (int)prods.size();
+            for (size_t i = 0; i < prods.size(); ++i) {
+                const Prod &q = prods[i];
+                f64_problem(l.p[i], *q.L, *q.R, q.M, q.N, q.K, q.sym, q.e);
+                if (q.patch)
+                    plan->patches.push_back({OP_F64, (int)plan->f64.size(), (int)i, q.patch});
+            }
+            plan->ops.push_back({OP_F64, (int)plan->f64.size(), 0});
+            plan->f64.push_back(l);
+            plan->kernel_launches += 1;
+            return true;
+        }
+        int bn = 128;
+        for (const Prod &q : prods)
+            if (q.N > 128)
+                bn = 256;
+        TcLaunch l;
+        std::memset(&l, 0, sizeof(l));
+        l.nprob = (int)prods.size();
+        int start = 0;
+        for (size_t i = 0; i < prods.size(); ++i) {
+            const Prod &q = prods[i];
+            if (!tc_problem(l.p[i], *q.L, *q.R, q.M, q.N, q.K, q.sym, q.e, bn))
+                return false;
+            l.tile_start[i] = start;
+            start += tc_num_tiles(l.p[i], bn);
+            if (q.patch)
+                plan->patches.push_back({OP_TC, (int)plan->tc.size(), (int)i, q.patch});
+        }
+        l.tile_start[prods.size()] = start;
+        // Algorithmic flops: 2 M N K per product, symmetric products counted at half;
+        // the hi/lo segments of FP32-class products are not counted again.
+        double fl = 0.0;
+        for (const Prod &q : prods)
+            fl += (q.sym ? 1.0 : 2.0) * (double)q.M * (double)q.N * (double)q.K;
+        plan->tc_flops.push_back(fl);
+        plan->ops.push_back({OP_TC, (int)plan->tc.size(), bn});
+        plan->tc.push_back(l);
+        plan->kernel_launches += 1;
+        plan->tc_launches_per_solve += 1;
+        return true;
+    }
+
+    bool build()
+    {
+        Plan &P = *plan;
+        const Layout &L = P.lay;
+        const Resolved &o = P.opt;
+        const bool f64 = o.prec == SVT_FP64;
+        const bool pairs = o.prec == SVT_FP32;
+        const bool skipP = o.mode == SVT_MODE_RANK_R;
+        const int M = (int)L.M, N = (int)L.N;
+
+        P.ops.push_back({OP_MEMSET, 0, 0});
+        P.ops.push_back({OP_REDUCE, 0, 0});
+        P.ops.push_back({OP_SPLIT, 0, 0});
+        P.kernel_launches += 2;
+
+        // Gram: S0 = Xt0 Xt0^T with FP64 diagonal colnorm2 / alpha^2 - tau^2 / alpha^2.
+        {
+            Buf Lg = L.Xt[0];
+            if (!f64 && !pairs) {  // BF16 tier keeps the lo part of X0^T separately
+                Lg.has_lo = true;
+                Lg.lo = L.XtLo0.hi;
+            }
+            Epi e = epi0();
+            set_out(e, L.S[0], pairs);
+            e.diag = reinterpret_cast<const double *>(base + L.colnorm);
+            e.dss = scal(SC_INV_ALPHA2);  // [INV_ALPHA2, TAU2_SCALED]
+            e.norm_acc = scal(SC_NRM_S0);
+            if (!emit({{&Lg, &Lg, N, N, M, true, e, 0}}))
+                return false;
+        }
+
+        // Chains.
+        int cur = 0;
+        for (int t = 0; t < o.iters; ++t) {
+            const double a = P.coef[3 * t], b = P.coef[3 * t + 1], c = P.coef[3 * t + 2];
+            const bool first = (t == 0);
+            const bool quintic = (o.schedule == SVT_SCHED_PE5) || (first && o.norm == SVT_NORM_GRAM);
+            const int nxt = 1 - cur;
+            // theta sources for the first step
+            const double *thP = nullptr, *thS = nullptr;
+            double powP = 0.5, powS = 0.5;
+            if (first) {
+                if (o.norm == SVT_NORM_FRO) {
+                    thP = scal(SC_NRM_X0);
+                    thS = scal(SC_NRM_S0);
+                } else {
+                    thP = scal(SC_NRM_YP);
+                    thS = scal(SC_NRM_YS);
+                    powP = powS = 0.25;
+                }
+            }
+            auto theta = [&](Epi &e, const double *src, double pw, double ea, double eb, double eg) {
+                if (!src)
+                    return;
+                e.theta_src = src;
+                e.theta_pow = pw;
+                e.ea = ea;
+                e.eb = eb;
+                e.eg = eg;
+            };
+            if (quintic) {
+                // Y = X^T X (P: Xt Xt^T; S: S S)
+                std::vector<Prod> s1;
+                if (!skipP) {
+                    Epi e = epi0();
+                    set_out(e, L.Yp, pairs);
+                    if (first && o.norm == SVT_NORM_GRAM)
+                        e.norm_acc = scal(SC_NRM_YP);
+                    s1.push_back({&L.Xt[cur], &L.Xt[cur], N, N, M, true, e, 0});
+                }
+                {
+                    Epi e = epi0();
+                    set_out(e, L.Ys, pairs);
+                    if (first && o.norm == SVT_NORM_GRAM)
+                        e.norm_acc = scal(SC_NRM_YS);
+                    s1.push_back({&L.S[cur], &L.S[cur], N, N, N, true, e, 0});
+                }
+                if (!emit(s1))
+                    return false;
+                // Z = c Y^2 + b Y + a I
+                std::vector<Prod> s2;
+                if (!skipP) {
+                    Epi e = epi0();
+                    e.alpha = c;
+                    e.gamma = a;
+                    set_c(e, L.Yp, b);
+                    set_out(e, L.Zp, pairs);
+                    theta(e, thP, powP, 5, 3, 1);
+                    s2.push_back({&L.Yp, &L.Yp, N, N, N, true, e, 0});
+                }
+                {
+                    Epi e = epi0();
+                    e.alpha = c;
+                    e.gamma = a;
+                    set_c(e, L.Ys, b);
+                    set_out(e, L.Zs, pairs);
+                    theta(e, thS, powS, 5, 3, 1);
+                    s2.push_back({&L.Ys, &L.Ys, N, N, N, true, e, 0});
+                }
+                if (!emit(s2))
+                    return false;
+            } else {
+                // cubic: Z = b Y + a I straight from the Y product
+                std::vector<Prod> s1;
+                if (!skipP) {
+                    Epi e = epi0();
+                    e.alpha = b;
+                    e.gamma = a;
+                    set_out(e, L.Zp, pairs);
+                    theta(e, thP, powP, 3, 0, 1);
+                    s1.push_back({&L.Xt[cur], &L.Xt[cur], N, N, M, true, e, 0});
+                }
+                {
+                    Epi e = epi0();
+                    e.alpha = b;
+                    e.gamma = a;
+                    set_out(e, L.Zs, pairs);
+                    theta(e, thS, powS, 3, 0, 1);
+                    s1.push_back({&L.S[cur], &L.S[cur], N, N, N, true, e, 0});
+                }
+                if (!emit(s1))
+                    return false;
+            }
+            // X <- X Z (P: also write X^T), S <- S Z (symmetric)
+            std::vector<Prod> s3;
+            if (!skipP) {
+                Epi e = epi0();
+                set_out(e, L.X[nxt], pairs);
+                set_t(e, L.Xt[nxt], pairs);
+                s3.push_back({&L.X[cur], &L.Zp, M, N, N, false, e, 0});
+            }
+            {
+                Epi e = epi0();
+                set_out(e, L.S[nxt], pairs);
+                s3.push_back({&L.S[cur], &L.Zs, N, N, N, true, e, 0});
+            }
+            if (!emit(s3))
+                return false;
+            cur = nxt;
+        }
+
+        // Polish (FP32-class): Z = 3/2 I - 1/2 X^T X; P' = X Z -> B = A - tau P'; S' = S Z.
+        if (o.polish || f64) {
+            std::vector<Prod> s1;
+            if (!skipP) {
+                Epi e = epi0();
+                e.alpha = -0.5;
+                e.gamma = 1.5;
+                set_out(e, L.ZPp, !f64);
+                s1.push_back({&L.Xt[cur], &L.Xt[cur], N, N, M, true, e, 0});
+            }
+            {
+                Epi e = epi0();
+                e.alpha = -0.5;
+                e.gamma = 1.5;
+                set_out(e, L.ZSp, !f64);
+                s1.push_back({&L.S[cur], &L.S[cur], N, N, N, true, e, 0});
+            }
+            if (!emit(s1))
+                return false;
+            std::vector<Prod> s2;
+            if (!skipP) {
+                Epi e = epi0();
+                e.alpha = -1.0;  // patched to -tau per call
+                e.beta = 1.0;    // C = A (patched)
+                e.c_kind = f64 ? C_F32 : C_F32;
+                e.c_trans = P.wide ? 1 : 0;
+                set_out(e, L.B, !f64);
+                s2.push_back({&L.X[cur], &L.ZPp, M, N, N, false, e, PT_C_IS_A | PT_ALPHA_NEG_TAU});
+            }
+            {
+                Epi e = epi0();
+                set_out(e, L.Sp, !f64);
+                s2.push_back({&L.S[cur], &L.ZSp, N, N, N, true, e, 0});
+            }
+            if (!emit(s2))
+                return false;
+            if (skipP) {
+                P.ops.push_back({OP_PREP, 1, 0});  // B = A (no P term)
+                P.kernel_launches += 1;
+            }
+        } else {
+            P.ops.push_back({OP_PREP, skipP ? 1 : 0, 0});  // B = A - tau X, S' = S
+            P.kernel_launches += 1;
+        }
+
+        // Combine: Y = 1/2 B S' + 1/2 B (FP32 out, transposed back for wide input).
+        {
+            Epi e = epi0();
+            e.alpha = 0.5;
+            set_c(e, L.B, 0.5);
+            e.o_kind = f64 ? O_F32 : O_F32;
+            e.o_trans = P.wide ? 1 : 0;
+            e.norm_acc = scal(SC_NRM_OUT);
+            if (!emit({{&L.B, &L.Sp, M, N, N, false, e, PT_O_IS_Y}}))
+                return false;
+        }
+        P.ops.push_back({OP_FINAL, 0, 0});
+        P.kernel_launches += 1;
+        return true;
+    }
+};
+
+// B = A_tall - tau * X (or A_tall alone), S' = S, when the polish is off or
+// the P chain is skipped.
+__global__ void prep_kernel(const float *__restrict__ A, int64_t lda, int wide, int64_t M,
+                            int64_t N, float tau, int xkind, const void *x0, const void *x1,
+                            int64_t ldx, int bkind, void *b0, void *b1, int64_t ldb,
+                            const void *s0, const void *s1, int skind, void *sp0, void *sp1,
+                            int64_t lds)
+{
+    const int64_t total = M * N;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / N, c = i % N;
+        double a = wide ? (double)A[c * lda + r] : (double)A[r * lda + c];
+        double x = 0.0;
+        if (xkind == C_BF16)
+            x = __bfloat162float(static_cast<const __nv_bfloat16 *>(x0)[r * ldx + c]);
+        else if (xkind == C_PAIR)
+            x = (double)__bfloat162float(static_cast<const __nv_bfloat16 *>(x0)[r * ldx + c]) +
+                (double)__bfloat162float(static_cast<const __nv_bfloat16 *>(x1)[r * ldx + c]);
+        else if (xkind == C_F64)
+            x = static_cast<const double *>(x0)[r * ldx + c];
+        double v = a - (double)tau * x;
+        if (bkind == O_F64) {
+            static_cast<double *>(b0)[r * ldb + c] = v;
+        } else {
+            __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
+            static_cast<__nv_bfloat16 *>(b0)[r * ldb + c] = hi;
+            static_cast<__nv_bfloat16 *>(b1)[r * ldb + c] =
+                __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
+        }
+        if (s0 && r < N) {
+            if (skind == C_F64) {
+                static_cast<double *>(sp0)[r * lds + c] = static_cast<const double *>(s0)[r * lds + c];
+            } else {
+                __nv_bfloat16 h = static_cast<const __nv_bfloat16 *>(s0)[r * lds + c];
+                __nv_bfloat16 l = (skind == C_PAIR) ? static_cast<const __nv_bfloat16 *>(s1)[r * lds + c]
+                                                    : __float2bfloat16_rn(0.0f);
+                static_cast<__nv_bfloat16 *>(sp0)[r * lds + c] = h;
+                static_cast<__nv_bfloat16 *>(sp1)[r * lds + c] = l;
+            }
+        }
+    }
+}
+
+
+} // namespace
+
+svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s)
+{
+    uint8_t *base = ctx->ws + P.ws_base;
+    const Layout &L = P.lay;
+    double *scal = reinterpret_cast<double *>(base + L.scal);
+    int *status = reinterpret_cast<int *>(base + L.status);
+    double *colnorm = reinterpret_cast<double *>(base + L.colnorm);
+    const bool f64 = P.opt.prec == SVT_FP64;
+    const bool pairs = P.opt.prec == SVT_FP32;
+    const bool skipP = P.opt.mode == SVT_MODE_RANK_R;
+    cudaError_t err = cudaSuccess;
+    int cur_final = P.opt.iters % 2;
+    for (const Op &op : P.ops) {
+        switch (op.kind) {
+        case OP_MEMSET:
+            // scalars, status and Gram diagonal are contiguous from L.scal
+            err = cudaMemsetAsync(base + L.scal, 0, L.colnorm + (size_t)L.N * sizeof(double) - L.scal, s);
+            break;
+        case OP_REDUCE:
+            err = ingest_reduce_launch(a.A, P.m, P.n, a.lda, P.wide ? 1 : 0, colnorm, scal, status, s);
+            break;
+        case OP_SPLIT: {
+            // same orientation as A: X (tall) when !wide, X^T when wide.
+            const Buf &same = P.wide ? L.Xt[0] : L.X[0];
+            const Buf &tran = P.wide ? L.X[0] : L.Xt[0];
+            void *same_lo = same.has_lo ? base + same.lo : nullptr;
+            void *tran_lo = tran.has_lo ? base + tran.lo : nullptr;
+            if (!f64 && !pairs) {  // BF16 tier: lo part of X0^T only, for the Gram
+                if (P.wide)
+                    same_lo = base + L.XtLo0.hi;
+                else
+                    tran_lo = base + L.XtLo0.hi;
+            }
+            err = ingest_split_launch(a.A, P.m, P.n, a.lda, a.tau, f64 ? 1 : 0, base + same.hi,
+                                      same_lo, same.ld, base + tran.hi, tran_lo, tran.ld, scal,
+                                      status, s);
+            break;
+        }
+        case OP_TC: {
+            TcLaunch l = P.tc[op.idx];
+            for (const PatchRec &pr : P.patches)
+                if (pr.kind == OP_TC && pr.launch == op.idx) {
+                    Epi &e = l.p[pr.prob].ep;
+                    if (pr.flags & PT_C_IS_A) {
+                        e.c0 = a.A;
+                        e.ldc = a.lda;
+                    }
+                    if (pr.flags & PT_O_IS_Y) {
+                        e.o0 = a.Y;
+                        e.ldo = a.ldy;
+                    }
+                    if (pr.flags & PT_ALPHA_NEG_TAU)
+                        e.alpha = -(double)a.tau;
+                }
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (ctx->profile) {
+                if (ctx->prof_next + 2 > ctx->prof_pool.size()) {
+                    for (int k = 0; k < 64; ++k) {
+                        cudaEvent_t ev;
+                        if (cudaEventCreate(&ev) != cudaSuccess)
+                            return SVT_ERR_CUDA;
+                        ctx->prof_pool.push_back(ev);
+                    }
+                }
+                e0 = ctx->prof_pool[ctx->prof_next++];
+                e1 = ctx->prof_pool[ctx->prof_next++];
+                cudaEventRecord(e0, s);
+            }
+            err = tc_gemm_launch(l, op.bn, ctx->num_sms, s);
+            if (ctx->profile) {
+                cudaEventRecord(e1, s);
+                ctx->prof_pending.push_back({e0, e1, P.tc_flops[op.idx]});
+            }
+            break;
+        }
+        case OP_F64: {
+            F64Launch l = P.f64[op.idx];
+            for (const PatchRec &pr : P.patches)
+                if (pr.kind == OP_F64 && pr.launch == op.idx) {
+                    Epi &e = l.p[pr.prob].ep;
+                    if (pr.flags & PT_C_IS_A) {
+                        e.c0 = a.A;
+                        e.ldc = a.lda;
+                    }
+                    if (pr.flags & PT_O_IS_Y) {
+                        e.o0 = a.Y;
+                        e.ldo = a.ldy;
+                    }
+                    if (pr.flags & PT_ALPHA_NEG_TAU)
+                        e.alpha = -(double)a.tau;
+                }
+            err = f64_gemm_launch(l, s);
+            break;
+        }
+        case OP_PREP: {
+            const Buf &X = L.X[cur_final];
+            const Buf &S = L.S[cur_final];
+            int xkind = (op.idx == 1 || skipP) ? C_NONE : (f64 ? C_F64 : (X.has_lo ? C_PAIR : C_BF16));
+            int skind = f64 ? C_F64 : (S.has_lo ? C_PAIR : C_BF16);
+            bool copyS = !(P.opt.polish || f64);
+            int64_t total = L.M * L.N;
+            int blocks = (int)std::min<int64_t>((total + 255) / 256, 4 * ctx->num_sms * 8);
+            prep_kernel<<<blocks, 256, 0, s>>>(
+                a.A, a.lda, P.wide ? 1 : 0, L.M, L.N, skipP ? 0.0f : a.tau, xkind,
+                xkind ? base + X.hi : nullptr, X.has_lo ? base + X.lo : nullptr, X.ld,
+                f64 ? O_F64 : O_PAIR, base + L.B.hi, f64 ? nullptr : base + L.B.lo, L.B.ld,
+                copyS ? base + S.hi : nullptr, (copyS && S.has_lo) ? base + S.lo : nullptr, skind,
+                base + L.Sp.hi, f64 ? nullptr : base + L.Sp.lo, L.Sp.ld);
+            err = cudaGetLastError();
+            break;
+        }
+        case OP_FINAL:
+            err = finalize_launch(scal, status, a.d_status, s);
+            break;
+        }
+        if (err != cudaSuccess)
+            return SVT_ERR_CUDA;
+    }
+    ctx->launches += (uint64_t)P.kernel_launches;
+    return SVT_OK;
+}
+
+svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_t ws_base,
+                    size_t ws_avail, Plan **out)
+{
+    Key k{m, n, r.iters, r.prec, r.schedule, r.norm, r.polish, r.mode, r.ell0, r.delta, ws_base};
+    auto it = ctx->plans.find(k);
+    if (it != ctx->plans.end()) {
+        *out = it->second.get();
+        return SVT_OK;
+    }
+    auto plan = std::make_unique<Plan>();
+    plan->m = m;
+    plan->n = n;
+    plan->wide = n > m;
+    plan->opt = r;
+    plan->lay = make_layout(m, n, r);
+    plan->ws_base = ws_base;
+    if (plan->lay.total > ws_avail)
+        return SVT_ERR_OOM;
+    plan->coef.assign((size_t)std::max(1, 3 * r.iters), 0.0);
+    if (schedule_coeffs(r.schedule, r.iters, r.ell0, r.delta, plan->coef.data()) != 0)
+        return SVT_ERR_INVALID;
+    Builder b{ctx, plan.get(), ctx->ws + ws_base, 256};
+    if (!b.build())
+        return SVT_ERR_CUDA;
+    *out = plan.get();
+    ctx->plans[k] = std::move(plan);
+    return SVT_OK;
+}
+
+svt_status plan_status_copy(svt_ctx *ctx, const Plan &P, int *host_dst, cudaStream_t s)
+{
+    const int *src = reinterpret_cast<const int *>(ctx->ws + P.ws_base + P.lay.status);
+    return cudaMemcpyAsync(host_dst, src, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess
+               ? SVT_OK
+               : SVT_ERR_CUDA;
+}
+
+static bool finite_tau(float tau) { return std::isfinite(tau) && tau >= 0.0f; }
+
+svt_status validate(const float *A, int64_t m, int64_t n, int64_t lda, float tau, const float *Y,
+                    int64_t ldy)
+{
+    if (!A || !Y || m <= 0 || n <= 0 || lda < n || ldy < n || !finite_tau(tau))
+        return SVT_ERR_INVALID;
+    if (m > (int64_t)1 << 20 || n > (int64_t)1 << 20)
+        return SVT_ERR_UNSUPPORTED;
+    // A and Y must not overlap
+    const char *a0 = reinterpret_cast<const char *>(A);
+    const char *a1 = reinterpret_cast<const char *>(A + (m - 1) * lda + n);
+    const char *y0 = reinterpret_cast<const char *>(Y);
+    const char *y1 = reinterpret_cast<const char *>(Y + (m - 1) * ldy + n);
+    if (a0 < y1 && y0 < a1)
+        return SVT_ERR_INVALID;
+    return SVT_OK;
+}
+
+} // namespace svt
+
+using namespace svt;
+
+extern "C" {
+
+const char *svt_status_str(svt_status s)
+{
+    switch (s) {
+    case SVT_OK: return "SVT_OK";
+    case SVT_ERR_INVALID: return "SVT_ERR_INVALID";
+    case SVT_ERR_OOM: return "SVT_ERR_OOM";
+    case SVT_ERR_CUDA: return "SVT_ERR_CUDA";
+    case SVT_ERR_NONFINITE: return "SVT_ERR_NONFINITE";
+    case SVT_ERR_DIVERGED: return "SVT_ERR_DIVERGED";
+    case SVT_ERR_TIMEOUT: return "SVT_ERR_TIMEOUT";
+    case SVT_ERR_NOT_READY: return "SVT_ERR_NOT_READY";
+    case SVT_ERR_BUSY: return "SVT_ERR_BUSY";
+    case SVT_ERR_UNSUPPORTED: return "SVT_ERR_UNSUPPORTED";
+    }
+    return "SVT_ERR_UNKNOWN";
+}
+
+void svt_options_default(svt_options *o)
+{
+    if (!o)
+        return;
+    o->iters = 20;
+    o->prec = SVT_BF16;
+    o->schedule = SVT_SCHED_AUTO;
+    o->norm = SVT_NORM_AUTO;
+    o->ell0 = 1e-3;
+    o->delta = -1.0;
+    o->polish = 1;
+    o->mode = SVT_MODE_SVT;
+}
+
+svt_status svt_workspace_bytes_ex(int64_t m, int64_t n, const svt_options *opt, size_t *out)
+{
+    Resolved r;
+    if (!out || m <= 0 || n <= 0 || !resolve(opt, &r))
+        return SVT_ERR_INVALID;
+    *out = make_layout(m, n, r).total;
+    return SVT_OK;
+}
+
+svt_status svt_workspace_bytes(int64_t m, int64_t n, svt_precision prec, size_t *out)
+{
+    svt_options o;
+    svt_options_default(&o);
+    o.prec = prec;
+    return svt_workspace_bytes_ex(m, n, &o, out);
+}
+
+svt_status svt_schedule_coeffs(svt_schedule_kind kind, int iters, double ell0, double delta,
+                               double *coef)
+{
+    int k = (kind == SVT_SCHED_NS3) ? SVT_SCHED_NS3 : SVT_SCHED_PE5;
+    if (kind != SVT_SCHED_AUTO && kind != SVT_SCHED_PE5 && kind != SVT_SCHED_NS3)
+        return SVT_ERR_INVALID;
+    return schedule_coeffs(k, iters, ell0, delta, coef) == 0 ? SVT_OK : SVT_ERR_INVALID;
+}
+
+svt_status svt_ctx_create(int device, void *workspace, size_t ws_bytes, svt_ctx_t *out)
+{
+    if (!out || (ws_bytes > 0 && !workspace) ||
+        (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0)
+        return SVT_ERR_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return SVT_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    auto *c = new svt_ctx();
+    c->device = device;
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return SVT_ERR_CUDA;
+    }
+    c->ws = static_cast<uint8_t *>(workspace);
+    c->ws_bytes = ws_bytes;
+    *out = c;
+    return SVT_OK;
+}
+
+svt_status svt_ctx_destroy(svt_ctx_t ctx)
+{
+    if (!ctx)
+        return SVT_ERR_INVALID;
+    serve_shutdown(ctx);
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (cudaEvent_t e : ctx->prof_pool)
+        cudaEventDestroy(e);
+    delete ctx;
+    return SVT_OK;
+}
+
+svt_status svt_polar_ex(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int64_t lda,
+                        float tau, const svt_options *opt, float *Y, int64_t ldy,
+                        svt_status *d_status, void *stream)
+{
+    if (!ctx)
+        return SVT_ERR_INVALID;
+    svt_status st = validate(A, m, n, lda, tau, Y, ldy);
+    if (st != SVT_OK)
+        return st;
+    Resolved r;
+    if (!resolve(opt, &r))
+        return SVT_ERR_INVALID;
+    if (r.prec == SVT_FP64 && (m > kF64MaxDim || n > kF64MaxDim))
+        return SVT_ERR_UNSUPPORTED;
+    if (serve_busy(ctx))
+        return SVT_ERR_BUSY;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    Plan *plan = nullptr;
+    st = get_plan(ctx, m, n, r, 0, ctx->ws_bytes, &plan);
+    if (st != SVT_OK)
+        return st;
+    CallArgs a{A, lda, tau, Y, ldy, d_status};
+    return run_plan(ctx, *plan, a, static_cast<cudaStream_t>(stream));
+}
+
+svt_status svt_polar(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int64_t lda, float tau,
+                     int iters, svt_precision prec, float *Y, int64_t ldy, svt_status *d_status,
+                     void *stream)
+{
+    svt_options o;
+    svt_options_default(&o);
+    o.iters = iters;
+    o.prec = prec;
+    return svt_polar_ex(ctx, A, m, n, lda, tau, &o, Y, ldy, d_status, stream);
+}
+
+svt_status svt_ctx_sync(svt_ctx_t ctx, void *stream)
+{
+    if (!ctx)
+        return SVT_ERR_INVALID;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    return SVT_OK;
+}
+
+uint64_t svt_ctx_launch_count(svt_ctx_t ctx) { return ctx ? ctx->launches : 0; }
+
+svt_status svt_ctx_profile(svt_ctx_t ctx, int enable)
+{
+    if (!ctx)
+        return SVT_ERR_INVALID;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->profile = enable != 0;
+    ctx->prof_pending.clear();
+    ctx->prof_next = 0;
+    return SVT_OK;
+}
+
+svt_status svt_ctx_profile_read(svt_ctx_t ctx, double *tc_ms, double *tc_flops,
+                                uint64_t *tc_launches)
+{
+    if (!ctx || !tc_ms || !tc_flops || !tc_launches)
+        return SVT_ERR_INVALID;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    double ms = 0.0, fl = 0.0;
+    for (auto &r : ctx->prof_pending) {
+        if (cudaEventSynchronize(r.b) != cudaSuccess)
+            return SVT_ERR_CUDA;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
+            return SVT_ERR_CUDA;
+        ms += t;
+        fl += r.flops;
+    }
+    *tc_ms = ms;
+    *tc_flops = fl;
+    *tc_launches = ctx->prof_pending.size();
+    ctx->prof_pending.clear();
+    ctx->prof_next = 0;
+    return SVT_OK;
+}
+
+svt_status svt_debug_gemm_bf16(svt_ctx_t ctx, int nseg, const void *L_hi, const void *L_lo,
+                               const void *R_hi, const void *R_lo, int64_t M, int64_t N,
+                               int64_t K, int64_t ldl, int64_t ldr, float *D, int64_t ldd,
+                               int sym, void *stream)
+{
+    if (!ctx || nseg < 1 || nseg > 3 || !L_hi || !R_hi || !D || M <= 0 || N <= 0 || K <= 0 ||
+        ldl < K || ldr < K || ldd < N || (ldl % 8) || (ldr % 8) || (sym && M != N))
+        return SVT_ERR_INVALID;
+    if ((nseg >= 2 && !R_lo) || (nseg == 3 && !L_lo))
+        return SVT_ERR_INVALID;
+    if (M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2)
+        return SVT_ERR_UNSUPPORTED;
+    const int bn = N > 128 ? 256 : 128;
+    TcLaunch l;
+    std::memset(&l, 0, sizeof(l));
+    l.nprob = 1;
+    TcProblem &p = l.p[0];
+    if (!encode_bf16_map(&p.mapL[0], L_hi, M, K, ldl, kBM) ||
+        !encode_bf16_map(&p.mapR[0], R_hi, N, K, ldr, bn))
+        return SVT_ERR_INVALID;
+    if (nseg >= 2 && !encode_bf16_map(&p.mapR[1], R_lo, N, K, ldr, bn))
+        return SVT_ERR_INVALID;
+    if (nseg == 3 && !encode_bf16_map(&p.mapL[1], L_lo, M, K, ldl, kBM))
+        return SVT_ERR_INVALID;
+    const int sl[3] = {0, 0, 1}, sr[3] = {0, 1, 0};
+    p.nseg = nseg;
+    for (int i = 0; i < nseg; ++i) {
+        p.segL[i] = sl[i];
+        p.segR[i] = sr[i];
+    }
+    p.M = (int)M;
+    p.N = (int)N;
+    p.K = (int)K;
+    p.sym = sym ? 1 : 0;
+    p.tiles_m = (int)((M + kBM - 1) / kBM);
+    p.tiles_n = (int)((N + bn - 1) / bn);
+    std::memset(&p.ep, 0, sizeof(p.ep));
+    p.ep.alpha = 1.0;
+    p.ep.o_kind = O_F32;
+    p.ep.o0 = D;
+    p.ep.ldo = ldd;
+    l.tile_start[0] = 0;
+    l.tile_start[1] = tc_num_tiles(p, bn);
+    if (cudaSetDevice(ctx->device) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    cudaError_t e = tc_gemm_launch(l, bn, ctx->num_sms, static_cast<cudaStream_t>(stream));
+    ctx->launches += 1;
+    return e == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;
+}
+
+} // extern "C"

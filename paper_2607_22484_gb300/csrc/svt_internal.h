@@ -1,0 +1,127 @@
+// Internal declarations shared by the libsvt translation units.
+//
+// The library computes singular value soft-thresholding (Eq. 1) through
+// Proposition 1 in its factored form A_tau = 1/2 (A - tau P)(I + S), with the
+// tall orientation M >= N: a wide input (n > m, the footnote's A A^T branch) is
+// solved as the tall problem of A^T and its result is stored transposed.
+//
+// Every dense product is D = sum_s L_s R_s^T with both operands K-major
+// (row-major, contraction along rows), and a fused epilogue
+//   v = alpha * D + beta * C + gamma * [r == c]
+// (alpha, beta, gamma optionally scaled by powers of a device-side norm), with
+// an FP64 diagonal override for the tau^2 shift and an FP64 sum of squares.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/svt.h"
+
+namespace svt {
+
+constexpr int kMaxProblems = 4;   // problems per by-value grouped launch
+constexpr int kBM = 128;          // tile rows (tcgen05 M)
+constexpr int kBK = 64;           // K per pipeline stage: one 128-byte swizzle row of BF16
+
+enum CKind : int { C_NONE = 0, C_BF16 = 1, C_PAIR = 2, C_F32 = 3, C_F64 = 4 };
+enum OKind : int { O_NONE = 0, O_BF16 = 1, O_PAIR = 2, O_F32 = 3, O_F64 = 4 };
+
+// Device-side scalar slots of one solve (FP64, in the workspace).
+enum Scal : int {
+    SC_NRM_A2 = 0,      // ||A||_F^2
+    SC_ALPHA = 1,       // power of two near ||A||_F; X0 = A / alpha exactly
+    SC_INV_ALPHA2 = 2,  // 1 / alpha^2
+    SC_TAU2_SCALED = 3, // tau^2 / alpha^2
+    SC_NRM_X0 = 4,      // ||X0||_F^2 = ||A||_F^2 / alpha^2
+    SC_NRM_S0 = 5,      // ||S0||_F^2 (S0 = (A^T A - tau^2 I) / alpha^2)
+    SC_NRM_YP = 6,      // ||X0^T X0||_F^2 of the P chain's first step
+    SC_NRM_YS = 7,      // ||S0^2||_F^2 of the S chain's first step
+    SC_NRM_OUT = 8,     // ||Y||_F^2 of the output
+    SC_COUNT = 16
+};
+
+struct Epi {
+    double alpha, beta, gamma;       // v = alpha D + beta C + gamma [r == c]
+    double ea, eb, eg;               // exponents: alpha *= theta^-ea, ...
+    const double *theta_src;         // theta = (*theta_src)^theta_pow; null: theta = 1
+    double theta_pow;
+    int c_kind, c_trans;             // C source; c_trans: C(r, c) = c0[c * ldc + r]
+    const void *c0, *c1;
+    int64_t ldc;
+    int o_kind, o_trans;             // output; o_trans: stored at [c * ldo + r]
+    void *o0, *o1;
+    int64_t ldo;
+    int t_kind;                      // extra transposed copy (O_NONE, O_BF16, O_PAIR, O_F64)
+    void *t0, *t1;
+    int64_t ldt;
+    double *norm_acc;                // += sum of v^2 over the full matrix
+    const double *diag;              // v(r, r) = diag[r] * dss[0] - dss[1] (FP64)
+    const double *dss;
+    int *status;                     // device status word of the solve
+};
+
+// One product of a grouped tensor-core launch.
+struct TcProblem {
+    CUtensorMap mapL[2];             // L operands, box 64 x 128
+    CUtensorMap mapR[2];             // R operands, box 64 x BN
+    int nseg;
+    int segL[3], segR[3];
+    int M, N, K;
+    int sym;                         // upper tiles only, mirrored store (M == N)
+    int tiles_m, tiles_n;
+    Epi ep;
+};
+
+struct TcLaunch {
+    int nprob;
+    int tile_start[kMaxProblems + 1];
+    TcProblem p[kMaxProblems];
+};
+
+// One product of the FP64 SIMT path: D = L R^T, L M x K (ldl), R N x K (ldr).
+struct F64Problem {
+    const double *L, *R;
+    int64_t ldl, ldr;
+    int M, N, K;
+    int sym;
+    Epi ep;
+};
+
+struct F64Launch {
+    int nprob;
+    F64Problem p[2];
+};
+
+// ---- launchers (defined in the .cu files) ----
+int tc_num_tiles(const TcProblem &p, int bn);
+cudaError_t tc_gemm_launch(const TcLaunch &l, int bn, int num_sms, cudaStream_t s);
+cudaError_t f64_gemm_launch(const F64Launch &l, cudaStream_t s);
+
+// Ingest: FP64 column norms of the tall matrix and ||A||_F^2.
+// wide = 0: tall matrix is A (M = m, N = n), colnorm2[j] = sum_i A[i][j]^2.
+// wide = 1: tall matrix is A^T (M = n, N = m), colnorm2[i] = sum_j A[i][j]^2.
+cudaError_t ingest_reduce_launch(const float *A, int64_t m, int64_t n, int64_t lda, int wide,
+                                 double *colnorm2, double *scal, int *status, cudaStream_t s);
+
+// Ingest: alpha = 2^round(log2 ||A||_F), X0 = A_tall / alpha written as
+//   xs (same orientation as A): hi (and lo when xs_lo), leading dim ld_s;
+//   xt (transposed): hi (and lo when xt_lo), leading dim ld_t;
+// in BF16 (f64 = 0) or FP64 (f64 = 1, hi only). Also fills the scalar slots.
+cudaError_t ingest_split_launch(const float *A, int64_t m, int64_t n, int64_t lda, float tau,
+                                int f64, void *xs_hi, void *xs_lo, int64_t ld_s, void *xt_hi,
+                                void *xt_lo, int64_t ld_t, double *scal, int *status,
+                                cudaStream_t s);
+
+// Final status: non-finite output norm -> DIVERGED (unless already set), then
+// copy the internal status word to the caller's (if any).
+cudaError_t finalize_launch(double *scal, int *status, svt_status *user_status, cudaStream_t s);
+
+// Host schedule (schedule.cpp).
+int schedule_coeffs(int kind, int iters, double ell0, double delta, double *coef);
+
+// Tensor-map encoder (driver entry point resolved through the runtime).
+bool encode_bf16_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld,
+                     int box_rows);
+
+} // namespace svt

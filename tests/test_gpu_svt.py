@@ -1,0 +1,160 @@
+"""End-to-end parity of the GPU polar SVT with the FP64 oracle, through the C ABI.
+
+Tolerances (relative Frobenius error against the oracle's A_tau, with tau at
+least 5 % of sigma_max away from every singular value): FP64 tier 1e-9, FP32
+tier 1e-4, BF16 tier 2e-2.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import schedule as osch
+from oracle import spectral
+import svt_workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+pkg = pytest.importorskip("paper_2607_22484_gb300")
+
+TOL = {"fp64": 1e-9, "fp32": 1e-4, "bf16": 2e-2}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return pkg.Context(0, workspace_bytes=64 << 20)
+
+
+def _run(ctx, a, tau, **opts):
+    dev = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    y = ctx.polar(dev, tau, status=status, **opts)
+    torch.cuda.synchronize()
+    return y.cpu().numpy().astype(np.float64), int(status.item())
+
+
+def _gap_matrix(m, n, seed, tau=0.3):
+    """Spectrum in [0.01, 1] with no value within 0.06 of tau."""
+    k = min(m, n)
+    rng = np.random.default_rng(seed)
+    lo = np.sort(rng.uniform(0.01, tau - 0.06, k // 2))
+    hi = np.sort(rng.uniform(tau + 0.06, 1.0, k - k // 2 - 1))
+    sig = np.sort(np.concatenate([lo, hi, [1.0]]))[::-1]
+    return wl.spectrum_matrix(sig, m, n, seed)
+
+
+def test_config_64_fp64_ns3(ctx):
+    a = wl.spectrum_64()
+    exact = oracle.svt_definition(a.astype(np.float64), 0.3)
+    y, st = _run(ctx, a, 0.3, iters=30, prec="fp64", schedule="ns3")
+    assert st == 0
+    assert oracle.relerr(y, exact) < TOL["fp64"] + 1e-7  # output is FP32: ~6e-8 rounding
+
+
+@pytest.mark.parametrize("prec,sched,iters", [("fp32", "ns3", 30), ("bf16", "pe5", 20),
+                                              ("fp32", "pe5", 20), ("bf16", "ns3", 30)])
+def test_config_64(ctx, prec, sched, iters):
+    a = wl.spectrum_64()
+    exact = oracle.svt_definition(a.astype(np.float64), 0.3)
+    y, st = _run(ctx, a, 0.3, iters=iters, prec=prec, schedule=sched)
+    assert st == 0
+    err = oracle.relerr(y, exact)
+    assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("shape", [(300, 200), (200, 300), (257, 257), (130, 390)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_shapes_branches(ctx, shape, prec):
+    a = _gap_matrix(*shape, seed=sum(shape))
+    exact = oracle.svt_definition(a.astype(np.float64), 0.3)
+    y, st = _run(ctx, a, 0.3, iters=30 if prec != "bf16" else 20, prec=prec,
+                 schedule="ns3" if prec == "fp64" else "pe5")
+    assert st == 0
+    err = oracle.relerr(y, exact)
+    tol = TOL[prec] if prec != "fp64" else 1e-6
+    assert err < tol, err
+
+
+def test_fp64_matches_spectral_model_unconverged(ctx):
+    """Few iterations: the FP64 tier equals the exact-arithmetic prediction."""
+    a = _gap_matrix(96, 64, seed=3)
+    u, s, v = oracle.jacobi_svd(a.astype(np.float64))
+    tau = 0.3
+    for sched, iters, norm in [("pe5", 3, "gram"), ("ns3", 5, "fro"), ("pe5", 4, "fro")]:
+        if sched == "pe5":
+            coefs, _ = osch.pe5_schedule(iters, 1e-3, 0.0)
+        else:
+            coefs = osch.ns3_schedule(iters)
+        pred = spectral.predict(u, s, v, tau, coefs, coefs, norm, norm, polish=True)
+        y, st = _run(ctx, a, tau, iters=iters, prec="fp64", schedule=sched, norm=norm)
+        assert st == 0
+        # output is stored as FP32
+        assert oracle.relerr(y, pred) < 1e-6, (sched, iters, norm)
+
+
+def test_tau_zero_and_large(ctx):
+    a = _gap_matrix(128, 96, seed=9)
+    y, st = _run(ctx, a, 0.0, iters=20, prec="fp32")
+    assert st == 0
+    assert oracle.relerr(y, a.astype(np.float64)) < 1e-4
+    y, st = _run(ctx, a, 1.5, iters=20, prec="bf16")
+    assert st == 0
+    assert np.linalg.norm(y) / np.linalg.norm(a) < 2e-2
+
+
+def test_nonfinite_input_reports_status(ctx):
+    a = _gap_matrix(64, 64, seed=1)
+    a[3, 5] = np.nan
+    _, st = _run(ctx, a, 0.3, iters=5, prec="bf16")
+    assert st == pkg.binding.ERR_NONFINITE
+
+
+def test_invalid_arguments(ctx):
+    a = torch.zeros(8, 8, device="cuda")
+    with pytest.raises(pkg.SVTError) as e:
+        ctx.polar(a, -1.0)
+    assert e.value.status == pkg.binding.ERR_INVALID
+    with pytest.raises(pkg.SVTError):
+        ctx.polar(a, float("nan"))
+    with pytest.raises(pkg.SVTError):
+        ctx.polar(a, 0.1, iters=-1)
+
+
+def test_svt_polar_basic_entry(ctx):
+    a = _gap_matrix(100, 80, seed=5)
+    exact = oracle.svt_definition(a.astype(np.float64), 0.3)
+    dev = torch.from_numpy(a).cuda()
+    y = ctx.polar_basic(dev, 0.3, iters=20, prec="bf16")
+    torch.cuda.synchronize()
+    assert oracle.relerr(y.cpu().numpy(), exact) < 2e-2
+
+
+def test_corollary_rank_r(ctx):
+    a = _gap_matrix(160, 128, seed=11)
+    u, s, v = oracle.jacobi_svd(a.astype(np.float64))
+    r = int(np.sum(s > 0.3))
+    exact = oracle.best_rank_r(a.astype(np.float64), r)
+    y, st = _run(ctx, a, 0.3, iters=20, prec="bf16", mode="rank_r")
+    assert st == 0
+    assert oracle.relerr(y, exact) < 2e-2
+
+
+def test_full_size_4096_known_spectrum(ctx):
+    """4096 x 4096 with a known SVD and a 6 % gap: BF16 result vs Eq. 1 by construction."""
+    n = 4096
+    rng = np.random.default_rng(77)
+    sig = np.concatenate([rng.uniform(0.36, 1.0, 300), rng.uniform(0.0, 0.24, n - 300)])
+    sig = np.sort(sig)[::-1]
+    sig[0] = 1.0
+    q1 = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    q2 = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    a = ((q1 * sig) @ q2.T).astype(np.float32)
+    exact = (q1 * np.maximum(sig - 0.3, 0)) @ q2.T
+    ctx.ensure_workspace(pkg.workspace_bytes(n, n, prec="bf16"))
+    y, st = _run(ctx, a, 0.3, iters=20, prec="bf16")
+    assert st == 0
+    err = oracle.relerr(y, exact)
+    print(f"4096^2 BF16 relerr {err:.3e}")
+    assert err < 2e-2
