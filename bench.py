@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Benchmark of polar-decomposition SVT on GB300.
+
+Workload (one step = one whole solve, every row of the hot path): A_tau of a
+4096 x 4096 matrix with iid N(0, 1/4096) entries (Marchenko-Pastur spectrum),
+tau = 0.5, BF16 tier: 20 Polar-Express-style quintic steps per chain plus one
+FP32-class polish step, FP32-class Gram and combine, FP64 norms and tau^2 shift.
+
+Prints ONE JSON line (rank 0). Multi-GPU runs (torchrun) are weak scaling:
+every rank solves its own matrix; ranks only meet at the barriers and the
+max-reduction of the timings.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (one-sided Jacobi SVD + Eq. 1) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SVT solves/s + % BF16 tensor peak vs plain FP32 path at relerr≤2e-2; p50/p99"
+N_DEFAULT = 4096
+TAU = 0.5
+ITERS = 20
+FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def workload_name(n):
+    return (f"polar SVT, {n}x{n} Marchenko-Pastur N(0,1/{n}), tau={TAU}, BF16 tier: "
+            f"{ITERS} Polar-Express-style steps per chain + FP32-class polish")
+
+
+def alg_flops(m, n, iters):
+    """Algorithmic flops of one solve (symmetric products counted at half):
+    BF16 steps iters * (3 M N^2 + 4 N^3), FP32-class Gram/polish/combine 6 M N^2 + 2 N^3."""
+    M, N = max(m, n), min(m, n)
+    return iters * (3 * M * N * N + 4 * N ** 3) + (6 * M * N * N + 2 * N ** 3)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self, t_start=None, t_end=None):
+        """Stop sampling; summarise the samples taken between t_start and t_end
+        (host time.time() values; None keeps all samples)."""
+        import datetime
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            if ts is not None and t_start is not None and not (t_start - 0.25 <= ts <= t_end + 0.25):
+                continue
+            try:
+                sm.append(float(parts[2]))
+                smax.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[6:10]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def oracle_sample(n, seed, rounds, repeats=1):
+    """Time the FP64 Jacobi oracle on a bounded sample of the workload.
+
+    Per repeat: the first `rounds` round-robin rounds of a Jacobi sweep on the
+    n x n workload matrix. Calibration (once): a full oracle solve of the 1024^2
+    instance of the same recipe and its first `rounds` rounds. One n x n solve is
+    estimated as T_full(1024) * [per-round(n) * rounds/sweep(n)] /
+    [per-round(1024) * rounds/sweep(1024)], i.e. the measured 1024^2 solve scaled
+    by the measured per-sweep cost ratio (sweep counts taken equal)."""
+    import numpy as np
+    import oracle
+    import svt_workloads as wl
+
+    def per_round(a):
+        t0 = time.perf_counter()
+        oracle.jacobi_svd(a, max_rounds=rounds, want_off=False)
+        return (time.perf_counter() - t0) / rounds
+
+    small = wl.marchenko_pastur(1024, seed=seed).astype(np.float64)
+    t0 = time.perf_counter()
+    _, _, _, info = oracle.jacobi_svd(small, return_info=True, want_off=False)
+    t_full_small = time.perf_counter() - t0
+    sweep_small = per_round(small) * 1023
+    a = wl.marchenko_pastur(n, seed=seed).astype(np.float64)
+    rps = n - 1 + (n & 1)
+    est = [t_full_small * (per_round(a) * rps) / sweep_small for _ in range(repeats)]
+    desc = (f"per step: the first {rounds} of the {rps} round-robin rounds of a one-sided Jacobi "
+            f"sweep on the {n}x{n} workload matrix; one solve estimated as the oracle's full "
+            f"1024x1024 solve of the same recipe ({t_full_small:.2f} s, {info['sweeps']} sweeps) "
+            f"scaled by the measured per-sweep cost ratio {n}^2 : 1024^2")
+    return est, desc, oracle.native.num_threads()
+
+
+def run_reference(args, n):
+    steps, warmup = args.steps, args.warmup
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    rounds = 16
+    est, desc, cores = oracle_sample(n, 1002, rounds, repeats=warmup + steps)
+    timed = est[warmup:]
+    per_solve = statistics.mean(timed)
+    value = 1.0 / per_solve
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": steps, "warmup": warmup, "ms_per_step": per_solve * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config(n),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": desc + f"; one sample per step ({rounds} rounds)"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config(n):
+    return {"workload": workload_name(n), "m": n, "n": n, "tau": TAU, "iters": ITERS,
+            "precision": "bf16", "schedule": "pe5", "polish": True,
+            "l2": "flushed between timed steps (512 MiB write outside the timed events)",
+            "parallelism": "replicas (independent matrices per GPU)"}
+
+
+# ------------------------------------------------------------- GPU arm
+
+def torch_plain_fp32(A, tau, coefs, theta_from="gram"):
+    """Comparator: the same method as plain PyTorch FP32 matmuls (TF32 off), one
+    matrix at a time, in the order of the paper's listing (Section 4)."""
+    import torch
+    m, n = A.shape
+
+    def polar(X, gram_first):
+        Y = X.mT @ X
+        th = torch.linalg.matrix_norm(Y).sqrt() if gram_first else torch.linalg.matrix_norm(X)
+        X = X / th
+        for a, b, c in coefs:
+            Y = X.mT @ X
+            X = X @ (a * torch.eye(X.shape[1], device=X.device) + b * Y + c * (Y @ Y))
+        Y = X.mT @ X
+        return X @ (1.5 * torch.eye(X.shape[1], device=X.device) - 0.5 * Y)
+
+    P = polar(A, True)
+    G = A.mT @ A - tau * tau * torch.eye(n, device=A.device)
+    S = polar(G, True)
+    return 0.5 * (A - tau * P) @ (torch.eye(n, device=A.device) + S)
+
+
+def run_ours(args, n):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2607_22484_gb300 as pkg
+    import svt_workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    A_np = wl.marchenko_pastur(n, seed=1002 + rank)
+    A = torch.from_numpy(A_np).to(dev)
+    Y = torch.empty_like(A)
+    ctx = pkg.Context(local, workspace_bytes=pkg.workspace_bytes(n, n, iters=ITERS, prec="bf16"))
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    opts = dict(iters=ITERS, prec="bf16")
+
+    sampler = ClockSampler(local)
+    sampler.start()  # started before the warm-up so its start-up cost is outside the timed region
+    for _ in range(args.warmup):
+        ctx.polar(A, TAU, out=Y, status=status, **opts)
+    torch.cuda.synchronize()
+
+    steps = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    launches0 = ctx.launch_count()
+    ctx.profile(True)
+    barrier()
+    torch.cuda.synchronize()
+    t_start = time.time()
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        ctx.polar(A, TAU, out=Y, status=status, **opts)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    t_end = time.time()
+    barrier()
+    if t_end - t_start < 0.5:  # make sure the sampler sees the timed region at least once
+        time.sleep(0.3)
+    clocks = sampler.stop(t_start, t_end)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tc_ms, tc_flops, tc_n = ctx.profile_read()
+    ctx.profile(False)
+    launches = ctx.launch_count() - launches0
+    st = int(status.item())
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = steps * world / (total_ms / 1e3)
+    if args.only_timed:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s",
+                              "ms_per_step": total_ms / steps, "only_timed": True}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # End to end through the public API with host buffers (pinned), copies timed.
+    A_host = torch.from_numpy(A_np).pin_memory()
+    Y_host = torch.empty_like(A_host).pin_memory()
+    ctx.polar_host(A_host, TAU, out_host=Y_host, **opts)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(steps, 10))
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(e2e_steps)]
+    barrier()
+    for i in range(e2e_steps):
+        flush.fill_(float(i))
+        e2e_ev[i][0].record()
+        ctx.polar_host(A_host, TAU, out_host=Y_host, **opts)
+        e2e_ev[i][1].record()
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = e2e_steps * world / (e2e_ms / 1e3)
+    finite = bool(torch.isfinite(Y_host).all().item())
+
+    # The library's FP32-class tier and a plain PyTorch FP32 comparator (same schedule).
+    fp32_steps = 3
+    ctx.polar(A, TAU, out=Y, iters=ITERS, prec="fp32")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(fp32_steps):
+        ctx.polar(A, TAU, out=Y, iters=ITERS, prec="fp32")
+    e1.record()
+    torch.cuda.synchronize()
+    fp32_tier = fp32_steps / (e0.elapsed_time(e1) / 1e3)
+    coefs = [tuple(r) for r in pkg.schedule_coeffs("pe5", ITERS, 1e-3, 1e-4)]
+    prev_tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    torch_plain_fp32(A, TAU, coefs)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(2):
+        torch_plain_fp32(A, TAU, coefs)
+    e1.record()
+    torch.cuda.synchronize()
+    torch.backends.cuda.matmul.allow_tf32 = prev_tf32
+    plain = 2 / (e0.elapsed_time(e1) / 1e3)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, src = load_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    achieved = (tc_flops / tc_n) / ((tc_ms / tc_n) / 1e3) / 1e12 if tc_n else 0.0
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "tc_gemm_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tr = json.load(f)
+        src_sha = hashlib.sha256(open(os.path.join(
+            ROOT, "paper_2607_22484_gb300", "csrc", "gemm_tc.cu"), "rb").read()).hexdigest()
+        if tr.get("gemm_tc_sha256") == src_sha and tr.get("n") == n:
+            traffic = tr.get("dram_bytes_per_launch")
+    lat = sorted(step_ms)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    fl = alg_flops(n, n, ITERS)
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": config(n),
+        "latency_ms": {"p50": p50, "p99": p99},
+        "step_tflops": fl / (total_ms / steps / 1e3) / 1e12,
+        "roofline": {"bound": "tensor", "kernel": "tc_gemm_kernel", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": f"{src} bf16_tflops_sustained", "traffic": traffic,
+                     "launches": tc_n, "kernel_ms_total": tc_ms},
+        "vs_fp32": {"library_fp32_tier_solves_per_s": fp32_tier,
+                    "torch_plain_fp32_solves_per_s": plain,
+                    "speedup_vs_library_fp32_tier": value / world / fp32_tier,
+                    "speedup_vs_torch_plain_fp32": value / world / plain},
+        "e2e": {"value": e2e_value, "unit": "solves/s",
+                "h2d_bytes_per_step": n * n * 4, "d2h_bytes_per_step": n * n * 4},
+        "gpu_launches": launches,
+        "status": pkg.status_str(st), "output_finite": finite,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        est, desc, cores = oracle_sample(n, 1002, 96, repeats=1)
+        line["cpu_baseline"] = {"value": 1.0 / est[0], "unit": "solves/s", "cores": cores,
+                                "kind": "oracle", "sample": desc}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="run only the warm-up and timed solves (for profiler launch lists)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args, args.size)
+    return run_ours(args, args.size)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -99,6 +99,12 @@ typedef struct {
                                    (default 1; ignored for SVT_FP64, which
                                    polishes in FP64) */
     svt_mode mode;              /* default SVT_MODE_SVT */
+    int hp_steps;               /* SVT_BF16 only: number of leading S-chain steps run
+                                   in the FP32-class tier (the shifted Gram's small
+                                   eigenvalues sigma^2 - tau^2 do not survive BF16
+                                   rounding until the iteration has spread them);
+                                   -1 (default) = every step whose design interval
+                                   starts below 0.1 */
 } svt_options;
 
 typedef struct svt_ctx *svt_ctx_t;

@@ -54,8 +54,11 @@ def num_threads() -> int:
 
 
 def jacobi_svd(a: np.ndarray, eps: float = 0.0, max_sweeps: int = 60, nthreads: int = 0,
-               return_info: bool = False, max_rounds: int = 0):
+               return_info: bool = False, max_rounds: int = 0, want_off: bool = True):
     """Thin SVD ``a = U diag(sigma) V^T`` of a real matrix by one-sided Jacobi in FP64.
+
+    ``max_rounds`` bounds the work (a timing sample); ``want_off`` = False skips the
+    final all-pairs orthogonality diagnostic (reported as NaN then).
 
     Works on ``a`` when m >= n and on ``a.T`` otherwise (then U and V swap), so U
     is m x k, V is n x k with k = min(m, n), sigma descending.
@@ -76,7 +79,9 @@ def jacobi_svd(a: np.ndarray, eps: float = 0.0, max_sweeps: int = 60, nthreads: 
     rc = _load().oracle_jacobi_svd(
         mm, nn, w.ctypes.data_as(dp), sigma.ctypes.data_as(dp), u.ctypes.data_as(dp),
         v.ctypes.data_as(dp), float(eps), int(max_sweeps), int(max_rounds), int(nthreads),
-        ctypes.byref(sweeps), ctypes.byref(off))
+        ctypes.byref(sweeps), ctypes.byref(off) if want_off else None)
+    if not want_off:
+        off = ctypes.c_double(float("nan"))
     if rc < 0:
         raise ValueError("oracle_jacobi_svd: bad arguments")
     if wide:

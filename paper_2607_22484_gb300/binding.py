@@ -45,7 +45,7 @@ EXPORTS = [
 class Options(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("prec", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("norm", ctypes.c_int), ("ell0", ctypes.c_double), ("delta", ctypes.c_double),
-                ("polish", ctypes.c_int), ("mode", ctypes.c_int)]
+                ("polish", ctypes.c_int), ("mode", ctypes.c_int), ("hp_steps", ctypes.c_int)]
 
 
 class Matrix(ctypes.Structure):
@@ -120,7 +120,7 @@ def _check(st: int, where: str):
 
 
 def make_options(iters: int = 20, prec="bf16", schedule="auto", norm="auto", ell0: float = 1e-3,
-                 delta: float = -1.0, polish: bool = True, mode="svt") -> Options:
+                 delta: float = -1.0, polish: bool = True, mode="svt", hp_steps: int = -1) -> Options:
     o = Options()
     lib().svt_options_default(ctypes.byref(o))
     o.iters = int(iters)
@@ -131,6 +131,7 @@ def make_options(iters: int = 20, prec="bf16", schedule="auto", norm="auto", ell
     o.delta = float(delta)
     o.polish = 1 if polish else 0
     o.mode = MODE[mode] if isinstance(mode, str) else int(mode)
+    o.hp_steps = int(hp_steps)
     return o
 
 
@@ -223,6 +224,28 @@ class Context:
                "svt_polar_ex")
         return out
 
+    def polar_host(self, A_host, tau: float, out_host=None, stream=None, **opts):
+        """A_tau of a host (ideally pinned) FP32 matrix: copy in, solve, copy out.
+
+        The device buffers are cached per shape; the copies and the solve are
+        ordered on one stream, and the call returns after the result is on the host."""
+        import torch
+        if A_host.is_cuda or A_host.dim() != 2 or A_host.dtype != torch.float32:
+            raise ValueError("A_host must be a 2-D float32 host tensor")
+        key = tuple(A_host.shape)
+        cache = self.__dict__.setdefault("_host_bufs", {})
+        if key not in cache:
+            dev = torch.device(f"cuda:{self.device}")
+            cache[key] = (torch.empty(key, dtype=torch.float32, device=dev),
+                          torch.empty(key, dtype=torch.float32, device=dev))
+        a_dev, y_dev = cache[key]
+        if out_host is None:
+            out_host = torch.empty(key, dtype=torch.float32, pin_memory=True)
+        a_dev.copy_(A_host, non_blocking=True)
+        self.polar(a_dev, tau, out=y_dev, stream=stream, **opts)
+        out_host.copy_(y_dev, non_blocking=True)
+        return out_host
+
     def polar_basic(self, A, tau: float, iters: int, prec="bf16", out=None, status=None,
                     stream=None):
         """The svt_polar entry point (default options apart from iters and precision)."""
@@ -250,6 +273,58 @@ class Context:
                                          ctypes.c_void_p(_stream_ptr(stream))),
                "svt_debug_gemm_bf16")
         return D
+
+    def _matrix(self, A, tau, out, status, opts):
+        import torch
+        a_ptr, m, n, lda = _f32_matrix(A, "A")
+        y_ptr, ym, yn, ldy = _f32_matrix(out, "out")
+        if (ym, yn) != (m, n):
+            raise ValueError("out has the wrong shape")
+        mat = Matrix()
+        mat.A, mat.m, mat.n, mat.lda = a_ptr, m, n, lda
+        mat.tau = float(tau)
+        mat.Y, mat.ldy = y_ptr, ldy
+        mat.opt = make_options(**opts)
+        mat.d_status = status.data_ptr() if status is not None else None
+        return mat
+
+    def batch(self, As, taus, outs=None, statuses=None, stream=None, opts=None):
+        """A_tau for each matrix of the list through svt_batch (asynchronous)."""
+        import torch
+        count = len(As)
+        if outs is None:
+            outs = [torch.empty_like(a) for a in As]
+        opts = opts or [{}] * count
+        if isinstance(opts, dict):
+            opts = [opts] * count
+        arr = (Matrix * count)()
+        for i in range(count):
+            arr[i] = self._matrix(As[i], taus[i], outs[i],
+                                  statuses[i] if statuses is not None else None, opts[i])
+        need = ctypes.c_size_t(0)
+        _check(lib().svt_batch_workspace_bytes(arr, count, ctypes.byref(need)),
+               "svt_batch_workspace_bytes")
+        self.ensure_workspace(int(need.value))
+        _check(lib().svt_batch(self.handle, arr, count, ctypes.c_void_p(_stream_ptr(stream))),
+               "svt_batch")
+        return outs
+
+    def submit(self, A, tau, out, status=None, **opts) -> int:
+        """Queue one serving request (svt_serve_submit); returns its ticket."""
+        mat = self._matrix(A, tau, out, status, opts)
+        t = ctypes.c_uint64(0)
+        _check(lib().svt_serve_submit(self.handle, ctypes.byref(mat), ctypes.byref(t)),
+               "svt_serve_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """(status, latency_ms); status ERR_NOT_READY while pending."""
+        lat = ctypes.c_double(0.0)
+        st = lib().svt_serve_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(lat))
+        return int(st), lat.value
+
+    def release(self, ticket: int):
+        return int(lib().svt_serve_release(self.handle, ctypes.c_uint64(ticket)))
 
     def sync(self, stream=None):
         _check(lib().svt_ctx_sync(self.handle, ctypes.c_void_p(_stream_ptr(stream))), "svt_ctx_sync")

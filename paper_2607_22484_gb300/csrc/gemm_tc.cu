@@ -236,133 +236,209 @@ __device__ __forceinline__ EpiScales epi_scales(const Epi &e)
     return s;
 }
 
-__device__ __forceinline__ float load_c(const Epi &e, int64_t r, int64_t c)
+// C(r, c0 + i) for i < 32 into cv (zero outside the matrix), vectorised where the
+// row segment is contiguous and aligned.
+__device__ __forceinline__ void load_c32(const Epi &e, int64_t r, int64_t c0, int ncol, bool row_ok,
+                                         float *cv)
 {
-    int64_t off = e.c_trans ? c * e.ldc + r : r * e.ldc + c;
-    switch (e.c_kind) {
-    case C_BF16:
-        return __bfloat162float(static_cast<const __nv_bfloat16 *>(e.c0)[off]);
-    case C_PAIR:
-        return __bfloat162float(static_cast<const __nv_bfloat16 *>(e.c0)[off]) +
-               __bfloat162float(static_cast<const __nv_bfloat16 *>(e.c1)[off]);
-    case C_F32:
-        return static_cast<const float *>(e.c0)[off];
-    default:
-        return 0.0f;
-    }
-}
-
-__device__ __forceinline__ void store_val(int kind, void *p0, void *p1, int64_t off, float v)
-{
-    if (kind == O_BF16) {
-        static_cast<__nv_bfloat16 *>(p0)[off] = __float2bfloat16_rn(v);
-    } else if (kind == O_PAIR) {
-        __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        static_cast<__nv_bfloat16 *>(p0)[off] = hi;
-        static_cast<__nv_bfloat16 *>(p1)[off] = __float2bfloat16_rn(v - __bfloat162float(hi));
-    } else if (kind == O_F32) {
-        static_cast<float *>(p0)[off] = v;
-    }
-}
-
-// Row-major store of 32 consecutive values of one row, vectorised when the
-// whole chunk is in range and 16-byte aligned.
-__device__ __forceinline__ void store_row32(int kind, void *p0, void *p1, int64_t ld, int64_t r,
-                                            int64_t c0, const float *v, int ncol_valid,
-                                            uint32_t mask)
-{
-    int64_t off = r * ld + c0;
-    bool full = (ncol_valid == 32) && (mask == 0xffffffffu);
-    if (full && (kind == O_BF16 || kind == O_PAIR) && ((off & 7) == 0)) {
-        uint4 *dh = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(p0) + off);
-        uint4 *dl = (kind == O_PAIR)
-                        ? reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(p1) + off)
-                        : nullptr;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            __align__(16) __nv_bfloat16 hi[8];
-            __align__(16) __nv_bfloat16 lo[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                hi[i] = __float2bfloat16_rn(v[q * 8 + i]);
-                lo[i] = __float2bfloat16_rn(v[q * 8 + i] - __bfloat162float(hi[i]));
-            }
-            dh[q] = *reinterpret_cast<uint4 *>(hi);
-            if (dl)
-                dl[q] = *reinterpret_cast<uint4 *>(lo);
-        }
-        return;
-    }
-    if (full && kind == O_F32 && ((off & 3) == 0)) {
-        float4 *d = reinterpret_cast<float4 *>(static_cast<float *>(p0) + off);
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        return;
-    }
 #pragma unroll
     for (int i = 0; i < 32; ++i)
-        if (i < ncol_valid && ((mask >> i) & 1u))
-            store_val(kind, p0, p1, off + i, v[i]);
-}
-
-// Apply the epilogue to the 32 accumulators of row r, columns c0 .. c0 + 31.
-__device__ __forceinline__ void epilogue_chunk(const TcProblem &P, const EpiScales &s, int64_t r,
-                                               int64_t c0, float *v, double &nrm)
-{
-    const Epi &e = P.ep;
-    const bool row_ok = r < P.M;
-    const int64_t rem = (int64_t)P.N - c0;
-    int ncol = rem < 32 ? (int)rem : 32;
-    if (ncol < 0)
-        ncol = 0;
-    uint32_t mask = 0;
+        cv[i] = 0.0f;
+    if (!row_ok || e.c_kind == C_NONE)
+        return;
+    if (!e.c_trans) {
+        const int64_t off = r * e.ldc + c0;
+        if (ncol == 32 && (e.c_kind == C_BF16 || e.c_kind == C_PAIR) && (off & 7) == 0) {
+            const uint4 *h = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(e.c0) + off);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint4 u = __ldg(h + q);
+                const __nv_bfloat16 *b = reinterpret_cast<const __nv_bfloat16 *>(&u);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    cv[q * 8 + j] = __bfloat162float(b[j]);
+            }
+            if (e.c_kind == C_PAIR) {
+                const uint4 *l = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(e.c1) + off);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4 u = __ldg(l + q);
+                    const __nv_bfloat16 *b = reinterpret_cast<const __nv_bfloat16 *>(&u);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        cv[q * 8 + j] += __bfloat162float(b[j]);
+                }
+            }
+            return;
+        }
+        if (ncol == 32 && e.c_kind == C_F32 && (off & 3) == 0) {
+            const float4 *f = reinterpret_cast<const float4 *>(static_cast<const float *>(e.c0) + off);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float4 u = __ldg(f + q);
+                cv[4 * q] = u.x;
+                cv[4 * q + 1] = u.y;
+                cv[4 * q + 2] = u.z;
+                cv[4 * q + 3] = u.w;
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
-        int64_t c = c0 + i;
-        float x = s.alpha * v[i];
-        bool ok = row_ok && i < ncol && (!P.sym || r <= c);
-        if (ok) {
-            if (e.c_kind != C_NONE)
-                x += s.beta * load_c(e, r, c);
-            if (r == c) {
-                x += s.gamma;
-                if (e.diag)
-                    x = (float)(e.diag[r] * e.dss[0] - e.dss[1]);
+        if (i >= ncol)
+            continue;
+        const int64_t c = c0 + i;
+        const int64_t off = e.c_trans ? c * e.ldc + r : r * e.ldc + c;
+        float x;
+        if (e.c_kind == C_F32)
+            x = static_cast<const float *>(e.c0)[off];
+        else {
+            x = __bfloat162float(static_cast<const __nv_bfloat16 *>(e.c0)[off]);
+            if (e.c_kind == C_PAIR)
+                x += __bfloat162float(static_cast<const __nv_bfloat16 *>(e.c1)[off]);
+        }
+        cv[i] = x;
+    }
+}
+
+constexpr int kStagePitch = 33;  // floats per staging row: conflict-free by rows and by columns
+
+// Store a 32 x 32 block held in shared memory `st` (st[a][b] = value of tile
+// element (r0 + a, c0 + b)) to global memory, coalesced: warp lanes cover whole
+// row segments (8 rows x 64 B for BF16, 4 rows x 128 B for FP32 per instruction).
+//   trans = 0: element (r0 + a, c0 + b) -> p[(r0 + a) * ld + c0 + b];
+//              symdiag: the block sits on the diagonal and (a > b) takes st[b][a].
+//   trans = 1: element (r0 + b, c0 + a) -> p[(c0 + a) * ld + r0 + b].
+// Only elements with row < M and col < N (tile coordinates) are written.
+__device__ __forceinline__ void store_block(const float *st, int kind, void *p0, void *p1,
+                                            int64_t ld, int64_t r0, int64_t c0, int64_t M,
+                                            int64_t N, bool trans, bool symdiag, int lane)
+{
+    // output rows: tile rows (trans = 0) or tile columns (trans = 1)
+    const int64_t orow0 = trans ? c0 : r0, ocol0 = trans ? r0 : c0;
+    const int64_t orows = trans ? N : M, ocols = trans ? M : N;
+    if (kind == O_BF16 || kind == O_PAIR) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int a = k * 8 + (lane >> 2);  // output row within the block
+            const int q = lane & 3;             // 16-byte chunk: columns 8q .. 8q + 7
+            const int64_t R = orow0 + a;
+            float x[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int b = q * 8 + j;
+                int sa, sb;  // staging coordinates
+                if (trans) { sa = b; sb = a; }
+                else if (symdiag && a > b) { sa = b; sb = a; }
+                else { sa = a; sb = b; }
+                x[j] = st[sa * kStagePitch + sb];
             }
-            mask |= (1u << i);
-            if (e.norm_acc) {
-                double xd = (double)x;
-                nrm += (P.sym && r != c) ? 2.0 * xd * xd : xd * xd;
+            if (R >= orows)
+                continue;
+            const int64_t C = ocol0 + q * 8;
+            const int64_t off = R * ld + C;
+            if (C + 8 <= ocols && (off & 7) == 0) {
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+                    hw[j] = *reinterpret_cast<uint32_t *>(&h2);
+                    __nv_bfloat162 l2 = __floats2bfloat162_rn(x[2 * j] - __low2float(h2),
+                                                              x[2 * j + 1] - __high2float(h2));
+                    lw[j] = *reinterpret_cast<uint32_t *>(&l2);
+                }
+                *reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(p0) + off) =
+                    make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                if (kind == O_PAIR)
+                    *reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(p1) + off) =
+                        make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (C + j < ocols) {
+                        __nv_bfloat16 h = __float2bfloat16_rn(x[j]);
+                        static_cast<__nv_bfloat16 *>(p0)[off + j] = h;
+                        if (kind == O_PAIR)
+                            static_cast<__nv_bfloat16 *>(p1)[off + j] =
+                                __float2bfloat16_rn(x[j] - __bfloat162float(h));
+                    }
+                }
             }
         }
-        v[i] = x;
-    }
-    if (!row_ok)
-        return;
-    // Main output.
-    if (e.o_trans) {
+    } else if (kind == O_F32) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-            if ((mask >> i) & 1u)
-                store_val(e.o_kind, e.o0, e.o1, (c0 + i) * e.ldo + r, v[i]);
-    } else {
-        store_row32(e.o_kind, e.o0, e.o1, e.ldo, r, c0, v, ncol, mask);
-    }
-    // Mirror of a symmetric result: (c, r) for r < c.
-    if (P.sym) {
+        for (int k = 0; k < 8; ++k) {
+            const int a = k * 4 + (lane >> 3);
+            const int q = lane & 7;  // columns 4q .. 4q + 3
+            const int64_t R = orow0 + a;
+            float x[4];
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-            if (((mask >> i) & 1u) && (c0 + i) != r)
-                store_val(e.o_kind, e.o0, e.o1, (c0 + i) * e.ldo + r, v[i]);
-    }
-    // Extra transposed copy (X^T next to X).
-    if (e.t_kind != O_NONE) {
+            for (int j = 0; j < 4; ++j) {
+                const int b = q * 4 + j;
+                int sa, sb;
+                if (trans) { sa = b; sb = a; }
+                else if (symdiag && a > b) { sa = b; sb = a; }
+                else { sa = a; sb = b; }
+                x[j] = st[sa * kStagePitch + sb];
+            }
+            if (R >= orows)
+                continue;
+            const int64_t C = ocol0 + q * 4;
+            const int64_t off = R * ld + C;
+            if (C + 4 <= ocols && (off & 3) == 0) {
+                *reinterpret_cast<float4 *>(static_cast<float *>(p0) + off) =
+                    make_float4(x[0], x[1], x[2], x[3]);
+            } else {
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-            if ((mask >> i) & 1u)
-                store_val(e.t_kind, e.t0, e.t1, (c0 + i) * e.ldt + r, v[i]);
+                for (int j = 0; j < 4; ++j)
+                    if (C + j < ocols)
+                        static_cast<float *>(p0)[off + j] = x[j];
+            }
+        }
     }
+}
+
+// Epilogue of one 32 x 32 block: lane = tile row r (r0 + lane), columns c0 .. c0 + 31.
+// Values are computed in registers, staged in shared memory, then stored coalesced
+// to every requested destination: the output (row-major or transposed), the
+// extra transposed copy and, for symmetric products, the mirror.
+__device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiScales &s, int64_t r0,
+                                               int64_t c0, float *v, double &nrm, float *st,
+                                               int lane)
+{
+    const Epi &e = P.ep;
+    const int64_t r = r0 + lane;
+    const bool row_ok = r < P.M;
+    const int64_t rem = (int64_t)P.N - c0;
+    const int ncol = rem < 32 ? (int)rem : 32;
+    float cv[32];
+    load_c32(e, r, c0, ncol, row_ok, cv);
+    const bool diag_block = (r0 == c0);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int64_t c = c0 + i;
+        float x = s.alpha * v[i] + s.beta * cv[i];
+        if (diag_block && r == c) {
+            x += s.gamma;
+            if (e.diag)
+                x = (float)(e.diag[r] * e.dss[0] - e.dss[1]);
+        }
+        if (e.norm_acc && row_ok && i < ncol && (!P.sym || r <= c)) {
+            const double xd = (double)x;
+            nrm += (P.sym && r != c) ? 2.0 * xd * xd : xd * xd;
+        }
+        st[lane * kStagePitch + i] = x;
+    }
+    __syncwarp();
+    const bool symdiag = P.sym && diag_block;
+    if (e.o_kind != O_NONE)
+        store_block(st, e.o_kind, e.o0, e.o1, e.ldo, r0, c0, P.M, P.N, e.o_trans != 0, symdiag, lane);
+    if (P.sym && !diag_block)  // mirror of a block strictly above the diagonal
+        store_block(st, e.o_kind, e.o0, e.o1, e.ldo, r0, c0, P.M, P.N, true, false, lane);
+    if (e.t_kind != O_NONE)
+        store_block(st, e.t_kind, e.t0, e.t1, e.ldt, r0, c0, P.M, P.N, true, false, lane);
+    __syncwarp();
 }
 
 // --------------------------------------------------------------- kernel
@@ -377,7 +453,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     constexpr int B_BYTES = BN * kBK * 2;
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * A_BYTES;
-    uint64_t *full = reinterpret_cast<uint64_t *>(sB + STAGES * B_BYTES);
+    float *stage_all = reinterpret_cast<float *>(sB + STAGES * B_BYTES);
+    uint64_t *full = reinterpret_cast<uint64_t *>(stage_all + 4 * 32 * kStagePitch);
     uint64_t *empty = full + STAGES;
     uint64_t *tfull = empty + STAGES;
     uint64_t *tempty = tfull + 2;
@@ -421,12 +498,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         // ------------------------------------------------ TMA producer
         int stage = 0;
         uint32_t phase = 0;
-        bool issued[STAGES];
-        uint32_t issued_parity[STAGES];
-        for (int s = 0; s < STAGES; ++s) {
-            issued[s] = false;
-            issued_parity[s] = 0;
-        }
+        uint32_t issued = 0, issued_parity = 0;  // bit s: stage s loaded / parity of its last load
         bool ok = true;
         for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
             TileCoord tc = decode_tile<BN>(L, t);
@@ -445,8 +517,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                     mbar_expect_tx(&full[stage], (uint32_t)(A_BYTES + B_BYTES));
                     tma_load_2d(sA + stage * A_BYTES, mL, kb * kBK, tc.tm * kBM, &full[stage]);
                     tma_load_2d(sB + stage * B_BYTES, mR, kb * kBK, tc.tn * BN, &full[stage]);
-                    issued[stage] = true;
-                    issued_parity[stage] = phase;
+                    issued |= 1u << stage;
+                    issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
                     if (++stage == STAGES) {
                         stage = 0;
                         phase ^= 1u;
@@ -456,9 +528,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         }
         // Drain: the last copy into every stage must have landed before exit.
         for (int s = 0; s < STAGES; ++s)
-            if (issued[s]) {
+            if ((issued >> s) & 1u) {
                 volatile int no_abort = 0;
-                mbar_wait(&full[s], issued_parity[s], &no_abort, nullptr, kWaitTimeoutNs / 4);
+                mbar_wait(&full[s], (issued_parity >> s) & 1u, &no_abort, nullptr, kWaitTimeoutNs / 4);
             }
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------ MMA issuer
@@ -516,7 +588,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue
         const int quad = warp & 3;  // TMEM lane quadrant this warp may access
-        const int row_in_tile = quad * 32 + lane;
+        float *stage_buf = stage_all + (warp - 2) * 32 * kStagePitch;
         int buf = 0;
         uint32_t tphase = 0;
         int last_prob = -1;
@@ -533,7 +605,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             if (!mbar_wait(&tfull[buf], tphase, abort_flag, status0, kWaitTimeoutNs))
                 break;
             tc_fence_after();
-            const int64_t r = (int64_t)tc.tm * kBM + row_in_tile;
             const int64_t warp_row0 = (int64_t)tc.tm * kBM + quad * 32;
             double nrm = 0.0;
 #pragma unroll 1
@@ -546,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                     continue;
                 float v[32];
                 tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + ch * 32), v);
-                epilogue_chunk(P, sc, r, c0, v, nrm);
+                epilogue_block(P, sc, warp_row0, c0, v, nrm, stage_buf, lane);
             }
             if (P.ep.norm_acc) {
 #pragma unroll
@@ -577,7 +648,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 template <int BN, int STAGES>
 constexpr int smem_bytes()
 {
-    return STAGES * (kBM + BN) * kBK * 2 + 1024 /* alignment slack */ + 256 /* barriers */;
+    return STAGES * (kBM + BN) * kBK * 2 + 4 * 32 * kStagePitch * 4 /* epilogue staging */ +
+           1024 /* alignment slack */ + 256 /* barriers */;
 }
 
 template <int BN, int STAGES>

@@ -33,6 +33,7 @@ struct Resolved {
     double ell0, delta;
     int polish;
     int mode;
+    int hp_steps;   // leading S-chain steps in the FP32-class tier (BF16 tier)
 };
 
 bool resolve(const svt_options *in, Resolved *r);
@@ -77,6 +78,9 @@ struct Plan {
     Layout lay;
     size_t ws_base;
     std::vector<double> coef;
+    std::vector<double> lo;         // lower end of each step's design interval
+    int hp_steps_s = 0;             // leading S steps in the FP32-class tier
+    bool final_s_pair = false;      // final S iterate carries a lo part
     std::vector<Op> ops;
     std::vector<TcLaunch> tc;
     std::vector<F64Launch> f64;
@@ -88,14 +92,15 @@ struct Plan {
 
 struct Key {
     int64_t m, n;
-    int iters, prec, schedule, norm, polish, mode;
+    int iters, prec, schedule, norm, polish, mode, hp_steps;
     double ell0, delta;
     size_t ws_base;
     bool operator<(const Key &o) const
     {
-        return std::tie(m, n, iters, prec, schedule, norm, polish, mode, ell0, delta, ws_base) <
-               std::tie(o.m, o.n, o.iters, o.prec, o.schedule, o.norm, o.polish, o.mode, o.ell0,
-                        o.delta, o.ws_base);
+        return std::tie(m, n, iters, prec, schedule, norm, polish, mode, hp_steps, ell0, delta,
+                        ws_base) < std::tie(o.m, o.n, o.iters, o.prec, o.schedule, o.norm,
+                                            o.polish, o.mode, o.hp_steps, o.ell0, o.delta,
+                                            o.ws_base);
     }
 };
 

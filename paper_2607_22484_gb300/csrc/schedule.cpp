@@ -173,15 +173,19 @@ double remez_quintic(double lo, double hi, double coef[3])
 
 } // namespace
 
-int schedule_coeffs(int kind, int iters, double ell0, double delta, double *coef)
+int schedule_coeffs(int kind, int iters, double ell0, double delta, double *coef, double *lo_out)
 {
     if (iters < 0 || (iters > 0 && !coef))
         return 1;
     if (kind == SVT_SCHED_NS3) {
+        double lo = (ell0 > 0.0 && ell0 < 1.0) ? ell0 : 1e-3;
         for (int t = 0; t < iters; ++t) {
             coef[3 * t] = 1.5;
             coef[3 * t + 1] = -0.5;
             coef[3 * t + 2] = 0.0;
+            if (lo_out)
+                lo_out[t] = lo;
+            lo = 1.5 * lo - 0.5 * lo * lo * lo;  // the cubic is increasing on [0, 1]
         }
         return 0;
     }
@@ -190,6 +194,8 @@ int schedule_coeffs(int kind, int iters, double ell0, double delta, double *coef
     double lo = ell0, hi = 1.0;
     for (int t = 0; t < iters; ++t) {
         double c[3];
+        if (lo_out)
+            lo_out[t] = lo;
         double dhi = hi * (1.0 + delta);
         if (dhi - lo < kSwitchWidth) {
             c[0] = 15.0 / 8.0;

@@ -106,6 +106,9 @@ bool resolve(const svt_options *in, Resolved *r)
     if (o.mode != SVT_MODE_SVT && o.mode != SVT_MODE_RANK_R)
         return false;
     r->mode = o.mode;
+    if (o.hp_steps < -1)
+        return false;
+    r->hp_steps = (o.prec == SVT_BF16) ? o.hp_steps : 0;
     return true;
 }
 
@@ -160,15 +163,17 @@ Layout make_layout(int64_t m, int64_t n, const Resolved &r)
     }
     if (!f64 && !pairs)
         L.XtLo0 = make_buf(a, L.N, L.M, L.esz, false);
+    // S-chain buffers hold hi/lo pairs when any S step runs in the FP32-class tier.
+    const bool pairsS = pairs || (r.prec == SVT_BF16 && r.hp_steps != 0);
     for (int i = 0; i < 2; ++i)
-        L.S[i] = make_buf(a, L.N, L.N, L.esz, pairs);
+        L.S[i] = make_buf(a, L.N, L.N, L.esz, pairsS);
     if (!skipP) {
         L.Yp = make_buf(a, L.N, L.N, L.esz, pairs);
         L.Zp = make_buf(a, L.N, L.N, L.esz, pairs);
         L.ZPp = make_buf(a, L.N, L.N, L.esz, !f64);
     }
-    L.Ys = make_buf(a, L.N, L.N, L.esz, pairs);
-    L.Zs = make_buf(a, L.N, L.N, L.esz, pairs);
+    L.Ys = make_buf(a, L.N, L.N, L.esz, pairsS);
+    L.Zs = make_buf(a, L.N, L.N, L.esz, pairsS);
     L.ZSp = make_buf(a, L.N, L.N, L.esz, !f64);
     L.B = make_buf(a, L.M, L.N, L.esz, !f64);
     L.Sp = make_buf(a, L.N, L.N, L.esz, !f64);
@@ -332,6 +337,14 @@ struct Builder {
         return true;
     }
 
+    // The same buffer used with or without its lo part.
+    static Buf view(const Buf &b, bool pair)
+    {
+        Buf v = b;
+        v.has_lo = pair && b.has_lo;
+        return v;
+    }
+
     bool build()
     {
         Plan &P = *plan;
@@ -341,6 +354,26 @@ struct Builder {
         const bool pairs = o.prec == SVT_FP32;
         const bool skipP = o.mode == SVT_MODE_RANK_R;
         const int M = (int)L.M, N = (int)L.N;
+        // Leading S-chain steps run in the FP32-class tier: all of them in the FP32
+        // tier; in the BF16 tier the first hp_steps (auto: the steps whose design
+        // interval starts below 0.1, while the shifted Gram's small eigenvalues are
+        // still below BF16 resolution relative to the largest).
+        int hpS = 0;
+        if (pairs) {
+            hpS = o.iters;
+        } else if (o.prec == SVT_BF16) {
+            if (o.hp_steps >= 0) {
+                hpS = std::min(o.hp_steps, o.iters);
+            } else {
+                for (int t = 0; t < o.iters; ++t)
+                    if (P.lo[t] < 0.1)
+                        hpS = t + 1;
+            }
+        }
+        // S after t steps is a pair iff step t (its consumer) runs FP32-class.
+        auto s_pair = [&](int t) { return pairs || t < hpS; };
+        P.hp_steps_s = hpS;
+        P.final_s_pair = s_pair(o.iters);
 
         P.ops.push_back({OP_MEMSET, 0, 0});
         P.ops.push_back({OP_REDUCE, 0, 0});
@@ -355,7 +388,7 @@ struct Builder {
                 Lg.lo = L.XtLo0.hi;
             }
             Epi e = epi0();
-            set_out(e, L.S[0], pairs);
+            set_out(e, L.S[0], s_pair(0));
             e.diag = reinterpret_cast<const double *>(base + L.colnorm);
             e.dss = scal(SC_INV_ALPHA2);  // [INV_ALPHA2, TAU2_SCALED]
             e.norm_acc = scal(SC_NRM_S0);
@@ -370,6 +403,8 @@ struct Builder {
             const bool first = (t == 0);
             const bool quintic = (o.schedule == SVT_SCHED_PE5) || (first && o.norm == SVT_NORM_GRAM);
             const int nxt = 1 - cur;
+            const bool hp = s_pair(t);  // this S step in the FP32-class tier
+            const Buf Sc = view(L.S[cur], hp), Ysv = view(L.Ys, hp), Zsv = view(L.Zs, hp);
             // theta sources for the first step
             const double *thP = nullptr, *thS = nullptr;
             double powP = 0.5, powS = 0.5;
@@ -404,10 +439,10 @@ struct Builder {
                 }
                 {
                     Epi e = epi0();
-                    set_out(e, L.Ys, pairs);
+                    set_out(e, L.Ys, hp);
                     if (first && o.norm == SVT_NORM_GRAM)
                         e.norm_acc = scal(SC_NRM_YS);
-                    s1.push_back({&L.S[cur], &L.S[cur], N, N, N, true, e, 0});
+                    s1.push_back({&Sc, &Sc, N, N, N, true, e, 0});
                 }
                 if (!emit(s1))
                     return false;
@@ -426,10 +461,10 @@ struct Builder {
                     Epi e = epi0();
                     e.alpha = c;
                     e.gamma = a;
-                    set_c(e, L.Ys, b);
-                    set_out(e, L.Zs, pairs);
+                    set_c(e, Ysv, b);
+                    set_out(e, L.Zs, hp);
                     theta(e, thS, powS, 5, 3, 1);
-                    s2.push_back({&L.Ys, &L.Ys, N, N, N, true, e, 0});
+                    s2.push_back({&Ysv, &Ysv, N, N, N, true, e, 0});
                 }
                 if (!emit(s2))
                     return false;
@@ -448,9 +483,9 @@ struct Builder {
                     Epi e = epi0();
                     e.alpha = b;
                     e.gamma = a;
-                    set_out(e, L.Zs, pairs);
+                    set_out(e, L.Zs, hp);
                     theta(e, thS, powS, 3, 0, 1);
-                    s1.push_back({&L.S[cur], &L.S[cur], N, N, N, true, e, 0});
+                    s1.push_back({&Sc, &Sc, N, N, N, true, e, 0});
                 }
                 if (!emit(s1))
                     return false;
@@ -465,8 +500,8 @@ struct Builder {
             }
             {
                 Epi e = epi0();
-                set_out(e, L.S[nxt], pairs);
-                s3.push_back({&L.S[cur], &L.Zs, N, N, N, true, e, 0});
+                set_out(e, L.S[nxt], s_pair(t + 1));
+                s3.push_back({&Sc, &Zsv, N, N, N, true, e, 0});
             }
             if (!emit(s3))
                 return false;
@@ -474,6 +509,7 @@ struct Builder {
         }
 
         // Polish (FP32-class): Z = 3/2 I - 1/2 X^T X; P' = X Z -> B = A - tau P'; S' = S Z.
+        const Buf Sfin = view(L.S[cur], s_pair(o.iters));
         if (o.polish || f64) {
             std::vector<Prod> s1;
             if (!skipP) {
@@ -488,7 +524,7 @@ struct Builder {
                 e.alpha = -0.5;
                 e.gamma = 1.5;
                 set_out(e, L.ZSp, !f64);
-                s1.push_back({&L.S[cur], &L.S[cur], N, N, N, true, e, 0});
+                s1.push_back({&Sfin, &Sfin, N, N, N, true, e, 0});
             }
             if (!emit(s1))
                 return false;
@@ -505,7 +541,7 @@ struct Builder {
             {
                 Epi e = epi0();
                 set_out(e, L.Sp, !f64);
-                s2.push_back({&L.S[cur], &L.ZSp, N, N, N, true, e, 0});
+                s2.push_back({&Sfin, &L.ZSp, N, N, N, true, e, 0});
             }
             if (!emit(s2))
                 return false;
@@ -680,7 +716,7 @@ svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s)
             const Buf &X = L.X[cur_final];
             const Buf &S = L.S[cur_final];
             int xkind = (op.idx == 1 || skipP) ? C_NONE : (f64 ? C_F64 : (X.has_lo ? C_PAIR : C_BF16));
-            int skind = f64 ? C_F64 : (S.has_lo ? C_PAIR : C_BF16);
+            int skind = f64 ? C_F64 : (P.final_s_pair ? C_PAIR : C_BF16);
             bool copyS = !(P.opt.polish || f64);
             int64_t total = L.M * L.N;
             int blocks = (int)std::min<int64_t>((total + 255) / 256, 4 * ctx->num_sms * 8);
@@ -688,7 +724,7 @@ svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s)
                 a.A, a.lda, P.wide ? 1 : 0, L.M, L.N, skipP ? 0.0f : a.tau, xkind,
                 xkind ? base + X.hi : nullptr, X.has_lo ? base + X.lo : nullptr, X.ld,
                 f64 ? O_F64 : O_PAIR, base + L.B.hi, f64 ? nullptr : base + L.B.lo, L.B.ld,
-                copyS ? base + S.hi : nullptr, (copyS && S.has_lo) ? base + S.lo : nullptr, skind,
+                copyS ? base + S.hi : nullptr, (copyS && P.final_s_pair) ? base + S.lo : nullptr, skind,
                 base + L.Sp.hi, f64 ? nullptr : base + L.Sp.lo, L.Sp.ld);
             err = cudaGetLastError();
             break;
@@ -707,7 +743,8 @@ svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s)
 svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_t ws_base,
                     size_t ws_avail, Plan **out)
 {
-    Key k{m, n, r.iters, r.prec, r.schedule, r.norm, r.polish, r.mode, r.ell0, r.delta, ws_base};
+    Key k{m, n, r.iters, r.prec, r.schedule, r.norm, r.polish, r.mode, r.hp_steps, r.ell0, r.delta,
+          ws_base};
     auto it = ctx->plans.find(k);
     if (it != ctx->plans.end()) {
         *out = it->second.get();
@@ -723,7 +760,9 @@ svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_
     if (plan->lay.total > ws_avail)
         return SVT_ERR_OOM;
     plan->coef.assign((size_t)std::max(1, 3 * r.iters), 0.0);
-    if (schedule_coeffs(r.schedule, r.iters, r.ell0, r.delta, plan->coef.data()) != 0)
+    plan->lo.assign((size_t)std::max(1, r.iters), 0.0);
+    if (schedule_coeffs(r.schedule, r.iters, r.ell0, r.delta, plan->coef.data(),
+                        plan->lo.data()) != 0)
         return SVT_ERR_INVALID;
     Builder b{ctx, plan.get(), ctx->ws + ws_base, 256};
     if (!b.build())
@@ -795,6 +834,7 @@ void svt_options_default(svt_options *o)
     o->delta = -1.0;
     o->polish = 1;
     o->mode = SVT_MODE_SVT;
+    o->hp_steps = -1;
 }
 
 svt_status svt_workspace_bytes_ex(int64_t m, int64_t n, const svt_options *opt, size_t *out)

@@ -118,7 +118,10 @@ cudaError_t ingest_split_launch(const float *A, int64_t m, int64_t n, int64_t ld
 cudaError_t finalize_launch(double *scal, int *status, svt_status *user_status, cudaStream_t s);
 
 // Host schedule (schedule.cpp).
-int schedule_coeffs(int kind, int iters, double ell0, double delta, double *coef);
+// coef[3t..3t+2] = (a_t, b_t, c_t); lo_out (nullable) receives the lower end l_t of
+// the interval step t was designed for.
+int schedule_coeffs(int kind, int iters, double ell0, double delta, double *coef,
+                    double *lo_out = nullptr);
 
 // Tensor-map encoder (driver entry point resolved through the runtime).
 bool encode_bf16_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld,

@@ -1,0 +1,123 @@
+"""svt_batch and the serving loop through the C ABI: parity with the oracle, equality
+with the same solve alone, admission under a workspace budget, fault isolation."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import svt_workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+pkg = pytest.importorskip("paper_2607_22484_gb300")
+
+
+def _items(count, s_hi=384, seed=44):
+    return wl.batch_recipe(count=count, s_lo=96, s_hi=s_hi, seed=seed)
+
+
+def test_batch_matches_oracle_and_single():
+    items = _items(10)
+    ctx = pkg.Context(0, workspace_bytes=1 << 20)
+    As = [torch.from_numpy(it.matrix()).cuda() for it in items]
+    taus = [it.tau for it in items]
+    st = torch.zeros(len(items), dtype=torch.int32, device="cuda")
+    outs = ctx.batch(As, taus, statuses=[st[i:i + 1] for i in range(len(items))],
+                     opts={"iters": 20, "prec": "bf16"})
+    torch.cuda.synchronize()
+    assert st.cpu().tolist() == [0] * len(items)
+    single = pkg.Context(0, workspace_bytes=1 << 20)
+    for it, a, y in zip(items, As, outs):
+        ref = single.polar(a, it.tau, iters=20, prec="bf16")
+        torch.cuda.synchronize()
+        exact, (u, s, v) = oracle.svt_definition(it.matrix().astype(np.float64), it.tau,
+                                                 return_svd=True)
+        got = y.cpu().numpy().astype(np.float64)
+        assert oracle.relerr(got, ref.cpu().numpy()) < 1e-5
+        if oracle.gap(s, it.tau) >= 0.05:
+            assert oracle.relerr(got, exact) < 2e-2, (it.m, it.n)
+
+
+def _serve(ctx, items, tiers, statuses=None):
+    tickets, outs = [], []
+    for i, it in enumerate(items):
+        a = torch.from_numpy(it.matrix()).cuda()
+        y = torch.full_like(a, float("nan"))
+        st = statuses[i] if statuses is not None else None
+        tickets.append(ctx.submit(a, it.tau, y, status=st, iters=20, prec=tiers[i]))
+        outs.append((a, y))
+    results = {}
+    t0 = time.time()
+    while len(results) < len(tickets) and time.time() - t0 < 120:
+        for t in tickets:
+            if t in results:
+                continue
+            stt, lat = ctx.poll(t)
+            if stt != pkg.binding.ERR_NOT_READY:
+                results[t] = (stt, lat)
+        time.sleep(0.001)
+    assert len(results) == len(tickets), "serving did not finish"
+    return tickets, outs, results
+
+
+def test_serving_same_alone_and_in_mix():
+    items = _items(12, s_hi=512, seed=45)
+    tiers = ["bf16" if i % 3 else "fp32" for i in range(len(items))]
+    # budget: room for only a few requests at a time, so admission has to wait
+    need = max(pkg.workspace_bytes(it.m, it.n, prec=t) for it, t in zip(items, tiers))
+    ctx = pkg.Context(0, workspace_bytes=3 * need)
+    tickets, outs, results = _serve(ctx, items, tiers)
+    alone = pkg.Context(0, workspace_bytes=need)
+    lats = []
+    for it, tier, t, (a, y) in zip(items, tiers, tickets, outs):
+        stt, lat = results[t]
+        assert stt == 0, pkg.status_str(stt)
+        lats.append(lat)
+        ref = alone.polar(a, it.tau, iters=20, prec=tier)
+        torch.cuda.synchronize()
+        assert oracle.relerr(y.cpu().numpy(), ref.cpu().numpy()) < 1e-5
+        assert ctx.release(t) == 0
+    assert all(l > 0 for l in lats)
+
+
+def test_serving_poisoned_request_is_isolated():
+    items = _items(6, seed=46)
+    ctx = pkg.Context(0, workspace_bytes=256 << 20)
+    tickets, outs = [], []
+    for i, it in enumerate(items):
+        m = it.matrix()
+        if i == 2:
+            m[0, 0] = np.inf
+        a = torch.from_numpy(m).cuda()
+        y = torch.empty_like(a)
+        tickets.append(ctx.submit(a, it.tau, y, iters=10, prec="bf16"))
+        outs.append((a, y))  # A and Y must stay alive until the ticket completes
+    done = {}
+    t0 = time.time()
+    while len(done) < len(tickets) and time.time() - t0 < 60:
+        for t in tickets:
+            if t not in done:
+                st, _ = ctx.poll(t)
+                if st != pkg.binding.ERR_NOT_READY:
+                    done[t] = st
+        time.sleep(0.001)
+    for i, t in enumerate(tickets):
+        if i == 2:
+            assert done[t] == pkg.binding.ERR_NONFINITE
+        else:
+            assert done[t] == 0
+            assert torch.isfinite(outs[i][1]).all()
+
+
+def test_serving_rejects_oversized_and_invalid():
+    ctx = pkg.Context(0, workspace_bytes=1 << 20)
+    a = torch.zeros(2048, 2048, device="cuda")
+    y = torch.empty_like(a)
+    with pytest.raises(pkg.SVTError) as e:
+        ctx.submit(a, 0.5, y)
+    assert e.value.status == pkg.binding.ERR_OOM
+    with pytest.raises(pkg.SVTError) as e:
+        ctx.submit(a, -0.5, y)
+    assert e.value.status == pkg.binding.ERR_INVALID
