@@ -261,6 +261,36 @@ svt_status svt_ctx_profile(svt_ctx_t ctx, int enable);
 svt_status svt_ctx_profile_read(svt_ctx_t ctx, double *tc_ms, double *tc_flops,
                                 uint64_t *tc_launches);
 
+/*
+ * svt_polar_noalloc: the svt_polar_ex solve without any workspace from the
+ * caller and without allocating device memory. (The paper has no counterpart:
+ * this entry point exists for callers, not for the method.)
+ *
+ * For callers that cannot allocate device memory at call time -- code inside a
+ * framework that owns all device allocations through its own pool, loops that
+ * must not pay cudaMalloc's implicit synchronisation or risk an out-of-memory
+ * failure at run time -- and that have no workspace to lend. Scratch comes from
+ * one static device array of SVT_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU
+ * loading the library reserves until the process exits; enough for BF16 and
+ * FP32-tier solves up to about 768 x 768 and FP64-tier solves up to 512 x 512.
+ *
+ *   device: CUDA device to run on (made current for the call, then restored).
+ *   A, m, n, lda, tau, opt, Y, ldy, d_status, stream: as svt_polar_ex.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and sets up an internal context; make that first call
+ * before any stream capture. All calls share the one array and it keeps the
+ * last call's contents (the solve re-initialises what must start at zero), so
+ * calls whose GPU work overlaps -- on different streams or from different
+ * threads without ordering -- race and corrupt each other's results.
+ * Errors: as svt_polar_ex, plus SVT_ERR_UNSUPPORTED when the solve needs more
+ * than SVT_NOALLOC_SCRATCH_BYTES (see svt_workspace_bytes_ex) and
+ * SVT_ERR_INVALID for a device index outside [0, 64).
+ */
+#define SVT_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+svt_status svt_polar_noalloc(int device, const float *A, int64_t m, int64_t n, int64_t lda,
+                             float tau, const svt_options *opt, float *Y, int64_t ldy,
+                             svt_status *d_status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,8 +38,9 @@ EXPORTS = [
     "svt_ctx_create", "svt_ctx_destroy", "svt_polar", "svt_polar_ex", "svt_batch",
     "svt_batch_workspace_bytes", "svt_serve_submit", "svt_serve_poll", "svt_serve_release",
     "svt_ctx_sync", "svt_schedule_coeffs", "svt_debug_gemm_bf16", "svt_ctx_launch_count",
-    "svt_ctx_profile", "svt_ctx_profile_read",
+    "svt_ctx_profile", "svt_ctx_profile_read", "svt_polar_noalloc",
 ]
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class Options(ctypes.Structure):
@@ -100,6 +101,8 @@ def lib():
         L.svt_ctx_launch_count.argtypes = [vp]
         L.svt_ctx_launch_count.restype = ctypes.c_uint64
         L.svt_ctx_profile.argtypes = [vp, i32]
+        L.svt_polar_noalloc.argtypes = [i32, vp, i64, i64, i64, ctypes.c_float,
+                                        ctypes.POINTER(Options), vp, i64, vp, vp]
         L.svt_ctx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_uint64)]
@@ -150,6 +153,26 @@ def schedule_coeffs(kind="pe5", iters: int = 20, ell0: float = 1e-3, delta: floa
     _check(lib().svt_schedule_coeffs(k, int(iters), float(ell0), float(delta), buf),
            "svt_schedule_coeffs")
     return np.array(buf[: 3 * iters], dtype=np.float64).reshape(iters, 3)
+
+
+def polar_noalloc(A, tau: float, out=None, status=None, stream=None, **opts):
+    """Y = A_tau through svt_polar_noalloc: no workspace, no device allocation by
+    the library (scratch is a fixed 32 MiB device array shared by all calls).
+    ``out`` should be preallocated by callers that cannot allocate."""
+    import torch
+    a_ptr, m, n, lda = _f32_matrix(A, "A")
+    if out is None:
+        out = torch.empty((m, n), dtype=torch.float32, device=A.device)
+    y_ptr, ym, yn, ldy = _f32_matrix(out, "out")
+    if (ym, yn) != (m, n):
+        raise ValueError("out has the wrong shape")
+    o = make_options(**opts)
+    st_ptr = status.data_ptr() if status is not None else None
+    _check(lib().svt_polar_noalloc(A.device.index or 0, ctypes.c_void_p(a_ptr), m, n, lda,
+                                   ctypes.c_float(tau), ctypes.byref(o), ctypes.c_void_p(y_ptr),
+                                   ldy, ctypes.c_void_p(st_ptr),
+                                   ctypes.c_void_p(_stream_ptr(stream))), "svt_polar_noalloc")
+    return out
 
 
 def _stream_ptr(stream) -> int:
