@@ -109,6 +109,18 @@ __device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *m
         : "memory");
 }
 
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *smem_src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(smem_u32(smem_src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Shared-memory matrix descriptor for a K-major operand tile laid out by TMA
 // with 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
@@ -399,12 +411,91 @@ __device__ __forceinline__ void store_block(const float *st, int kind, void *p0,
     }
 }
 
+// Byte offset of element (row, col) of a 32 x 32 staging block laid out the way
+// the TMA unit reads it: FP32 rows of 128 B with the 128-byte swizzle (16-byte
+// chunk index XOR row % 8), BF16 rows of 64 B with the 64-byte swizzle (chunk
+// index XOR (row / 2) % 4). Both orders of writing -- a lane per row with 16-byte
+// vectors, or a lane per column with scalars -- are free of bank conflicts.
+__device__ __forceinline__ uint32_t stg_off_f32(int row, int col)
+{
+    return (uint32_t)(row * 128 + ((((col >> 2) ^ (row & 7))) << 4) + (col & 3) * 4);
+}
+__device__ __forceinline__ uint32_t stg_off_b16(int row, int col)
+{
+    return (uint32_t)(row * 64 + ((((col >> 3) ^ ((row >> 1) & 3))) << 4) + (col & 7) * 2);
+}
+
+// Stage the warp's 32 x 32 block (lane = block row, x[] = its 32 columns) and
+// store it with one or two TMA stores: at tile coordinates (x = c0, y = r0), or
+// transposed at (x = r0, y = c0). `kind` is O_F32, O_BF16 or O_PAIR (hi through
+// m0, lo through m1). stg0 / stg1 are 1024-byte aligned 4 KiB buffers of this warp.
+__device__ __forceinline__ void tma_store_block(const float *x, int kind, bool trans,
+                                                const CUtensorMap *m0, const CUtensorMap *m1,
+                                                int r0, int c0, uint8_t *stg0, uint8_t *stg1,
+                                                int lane)
+{
+    if (lane == 0)
+        bulk_wait_read0();  // previous stores from these buffers have read them
+    __syncwarp();
+    if (kind == O_F32) {
+        if (!trans) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                *reinterpret_cast<float4 *>(stg0 + stg_off_f32(lane, 4 * q)) =
+                    make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                *reinterpret_cast<float *>(stg0 + stg_off_f32(c, lane)) = x[c];
+        }
+    } else {
+        const bool pair = (kind == O_PAIR);
+        if (!trans) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(x[8 * q + 2 * j], x[8 * q + 2 * j + 1]);
+                    hw[j] = *reinterpret_cast<uint32_t *>(&h2);
+                    __nv_bfloat162 l2 = __floats2bfloat162_rn(x[8 * q + 2 * j] - __low2float(h2),
+                                                              x[8 * q + 2 * j + 1] - __high2float(h2));
+                    lw[j] = *reinterpret_cast<uint32_t *>(&l2);
+                }
+                *reinterpret_cast<uint4 *>(stg0 + stg_off_b16(lane, 8 * q)) =
+                    make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                if (pair)
+                    *reinterpret_cast<uint4 *>(stg1 + stg_off_b16(lane, 8 * q)) =
+                        make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                __nv_bfloat16 h = __float2bfloat16_rn(x[c]);
+                *reinterpret_cast<__nv_bfloat16 *>(stg0 + stg_off_b16(c, lane)) = h;
+                if (pair)
+                    *reinterpret_cast<__nv_bfloat16 *>(stg1 + stg_off_b16(c, lane)) =
+                        __float2bfloat16_rn(x[c] - __bfloat162float(h));
+            }
+        }
+    }
+    fence_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+        const int sx = trans ? r0 : c0, sy = trans ? c0 : r0;
+        tma_store_2d(m0, sx, sy, stg0);
+        if (kind == O_PAIR)
+            tma_store_2d(m1, sx, sy, stg1);
+        bulk_commit();
+    }
+}
+
 // Epilogue of one 32 x 32 block: lane = tile row r (r0 + lane), columns c0 .. c0 + 31.
 // Values are computed in registers, staged in shared memory, then stored coalesced
 // to every requested destination: the output (row-major or transposed), the
 // extra transposed copy and, for symmetric products, the mirror.
 __device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiScales &s, int64_t r0,
-                                               int64_t c0, float *v, double &nrm, float *st,
+                                               int64_t c0, float *v, double &nrm, uint8_t *stg,
                                                int lane)
 {
     const Epi &e = P.ep;
@@ -428,15 +519,39 @@ __device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiScal
             const double xd = (double)x;
             nrm += (P.sym && r != c) ? 2.0 * xd * xd : xd * xd;
         }
-        st[lane * kStagePitch + i] = x;
+        v[i] = x;
     }
-    __syncwarp();
     const bool symdiag = P.sym && diag_block;
-    if (e.o_kind != O_NONE)
+    uint8_t *stg0 = stg, *stg1 = stg + 4096;
+    // Outputs through TMA stores (all but diagonal blocks of symmetric products).
+    const bool o_tma = P.o_tma && e.o_kind != O_NONE && !symdiag;
+    if (o_tma)
+        tma_store_block(v, e.o_kind, e.o_trans != 0, &P.mapO[0], &P.mapO[1], (int)r0, (int)c0,
+                        stg0, stg1, lane);
+    if (P.sym && !diag_block && P.o_tma)  // mirror of a block strictly above the diagonal
+        tma_store_block(v, e.o_kind, true, &P.mapO[0], &P.mapO[1], (int)r0, (int)c0, stg0, stg1,
+                        lane);
+    if (P.t_tma && e.t_kind != O_NONE)
+        tma_store_block(v, e.t_kind, true, &P.mapT[0], &P.mapT[1], (int)r0, (int)c0, stg0, stg1,
+                        lane);
+    const bool need_plain = (e.o_kind != O_NONE && !o_tma) || (P.sym && !diag_block && !P.o_tma) ||
+                            (e.t_kind != O_NONE && !P.t_tma);
+    if (!need_plain)
+        return;
+    // Coalesced plain-store path: stage with a 33-float pitch, then whole row segments.
+    if (lane == 0)
+        bulk_wait_read0();
+    __syncwarp();
+    float *st = reinterpret_cast<float *>(stg);
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        st[lane * kStagePitch + i] = v[i];
+    __syncwarp();
+    if (e.o_kind != O_NONE && !o_tma)
         store_block(st, e.o_kind, e.o0, e.o1, e.ldo, r0, c0, P.M, P.N, e.o_trans != 0, symdiag, lane);
-    if (P.sym && !diag_block)  // mirror of a block strictly above the diagonal
+    if (P.sym && !diag_block && !P.o_tma)
         store_block(st, e.o_kind, e.o0, e.o1, e.ldo, r0, c0, P.M, P.N, true, false, lane);
-    if (e.t_kind != O_NONE)
+    if (e.t_kind != O_NONE && !P.t_tma)
         store_block(st, e.t_kind, e.t0, e.t1, e.ldt, r0, c0, P.M, P.N, true, false, lane);
     __syncwarp();
 }
@@ -453,8 +568,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     constexpr int B_BYTES = BN * kBK * 2;
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * A_BYTES;
-    float *stage_all = reinterpret_cast<float *>(sB + STAGES * B_BYTES);
-    uint64_t *full = reinterpret_cast<uint64_t *>(stage_all + 4 * 32 * kStagePitch);
+    uint8_t *stage_all = sB + STAGES * B_BYTES;  // 4 epilogue warps x 8 KiB, 1024-aligned
+    uint64_t *full = reinterpret_cast<uint64_t *>(stage_all + 4 * 8192);
     uint64_t *empty = full + STAGES;
     uint64_t *tfull = empty + STAGES;
     uint64_t *tempty = tfull + 2;
@@ -588,7 +703,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue
         const int quad = warp & 3;  // TMEM lane quadrant this warp may access
-        float *stage_buf = stage_all + (warp - 2) * 32 * kStagePitch;
+        uint8_t *stage_buf = stage_all + (warp - 2) * 8192;
         int buf = 0;
         uint32_t tphase = 0;
         int last_prob = -1;
@@ -633,6 +748,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 tphase ^= 1u;
             }
         }
+        // All TMA stores of this warp complete before the CTA may exit.
+        if (lane == 0)
+            bulk_wait_all0();
+        __syncwarp();
     }
 
     tc_fence_before();
@@ -648,7 +767,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 template <int BN, int STAGES>
 constexpr int smem_bytes()
 {
-    return STAGES * (kBM + BN) * kBK * 2 + 4 * 32 * kStagePitch * 4 /* epilogue staging */ +
+    return STAGES * (kBM + BN) * kBK * 2 + 4 * 8192 /* epilogue staging */ +
            1024 /* alignment slack */ + 256 /* barriers */;
 }
 

@@ -72,6 +72,49 @@ bool encode_bf16_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t co
     return r == CUDA_SUCCESS;
 }
 
+bool encode_store_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld,
+                      bool f32)
+{
+    std::call_once(g_encode_once, resolve_encode);
+    const int64_t esz = f32 ? 4 : 2;
+    if (!g_encode || !ptr || rows <= 0 || cols <= 0 || ((ld * esz) % 16) != 0 ||
+        (reinterpret_cast<uintptr_t>(ptr) & 15) != 0)
+        return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                          2, const_cast<void *>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          f32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+void attach_store_maps(TcProblem &p)
+{
+    const Epi &e = p.ep;
+    p.o_tma = 0;
+    p.t_tma = 0;
+    // Output: tile-oriented M x N, or transposed N x M when o_trans.
+    if (e.o_kind == O_BF16 || e.o_kind == O_PAIR || e.o_kind == O_F32) {
+        const bool f32 = e.o_kind == O_F32;
+        const int64_t rows = e.o_trans ? p.N : p.M, cols = e.o_trans ? p.M : p.N;
+        bool ok = encode_store_map(&p.mapO[0], e.o0, rows, cols, e.ldo, f32);
+        if (ok && e.o_kind == O_PAIR)
+            ok = encode_store_map(&p.mapO[1], e.o1, rows, cols, e.ldo, false);
+        p.o_tma = ok ? 1 : 0;
+    }
+    // Transposed copy: N x M.
+    if (e.t_kind == O_BF16 || e.t_kind == O_PAIR) {
+        bool ok = encode_store_map(&p.mapT[0], e.t0, p.N, p.M, e.ldt, false);
+        if (ok && e.t_kind == O_PAIR)
+            ok = encode_store_map(&p.mapT[1], e.t1, p.N, p.M, e.ldt, false);
+        p.t_tma = ok ? 1 : 0;
+    }
+}
+
 
 bool resolve(const svt_options *in, Resolved *r)
 {
@@ -260,6 +303,7 @@ struct Builder {
         p.tiles_m = (M + kBM - 1) / kBM;
         p.tiles_n = (N + bn - 1) / bn;
         p.ep = e;
+        attach_store_maps(p);
         return true;
     }
 
@@ -1023,6 +1067,7 @@ svt_status svt_debug_gemm_bf16(svt_ctx_t ctx, int nseg, const void *L_hi, const 
     p.ep.o_kind = O_F32;
     p.ep.o0 = D;
     p.ep.ldo = ldd;
+    attach_store_maps(p);
     l.tile_start[0] = 0;
     l.tile_start[1] = tc_num_tiles(p, bn);
     if (cudaSetDevice(ctx->device) != cudaSuccess)

@@ -20,7 +20,7 @@
 
 namespace svt {
 
-constexpr int kMaxProblems = 4;   // problems per by-value grouped launch
+constexpr int kMaxProblems = 2;   // problems per by-value grouped launch (P and S chains)
 constexpr int kBM = 128;          // tile rows (tcgen05 M)
 constexpr int kBK = 64;           // K per pipeline stage: one 128-byte swizzle row of BF16
 
@@ -65,6 +65,9 @@ struct Epi {
 struct TcProblem {
     CUtensorMap mapL[2];             // L operands, box 64 x 128
     CUtensorMap mapR[2];             // R operands, box 64 x BN
+    CUtensorMap mapO[2];             // output hi/lo (or FP32), box 32 x 32, for TMA stores
+    CUtensorMap mapT[2];             // transposed copy hi/lo, box 32 x 32
+    int o_tma, t_tma;                // 1: store through mapO / mapT
     int nseg;
     int segL[3], segR[3];
     int M, N, K;
@@ -123,8 +126,14 @@ cudaError_t finalize_launch(double *scal, int *status, svt_status *user_status, 
 int schedule_coeffs(int kind, int iters, double ell0, double delta, double *coef,
                     double *lo_out = nullptr);
 
-// Tensor-map encoder (driver entry point resolved through the runtime).
+// Tensor-map encoders (driver entry point resolved through the runtime).
+// Operand loads: BF16, box 64 (K) x box_rows, 128-byte swizzle.
 bool encode_bf16_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld,
                      int box_rows);
+// Epilogue stores: BF16 (64-byte swizzle) or FP32 (128-byte swizzle), box 32 x 32.
+bool encode_store_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld,
+                      bool f32);
+// Fill mapO / mapT of a problem from its epilogue's outputs where they qualify.
+void attach_store_maps(TcProblem &p);
 
 } // namespace svt
