@@ -8,10 +8,11 @@
 // c (X^T X)^2) of both polar chains, the polish step and the final combine
 // 1/2 (A - tau P)(I + S) of Proposition 1.
 //
-// Structure (persistent, one CTA per SM, 192 threads):
+// Structure (persistent, one CTA per SM, 320 threads):
 //   warp 0    : TMA producer (one thread), STAGES-deep shared-memory ring.
 //   warp 1    : tensor-memory allocator and MMA issuer (one thread).
-//   warps 2-5 : epilogue; warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31.
+//   warps 2-9 : epilogue; warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31, and
+//               the two warps of a lane quadrant take alternate 32-column chunks.
 // Two accumulator buffers of BN FP32 columns each let the epilogue of one tile
 // overlap the MMAs of the next.
 //
@@ -30,7 +31,8 @@ namespace svt {
 namespace {
 
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;  // 2 s
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;  // 2 producer/MMA warps + 8 epilogue warps
+constexpr int kEpiWarps = 8;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -248,37 +250,35 @@ __device__ __forceinline__ EpiScales epi_scales(const Epi &e)
     return s;
 }
 
-// C(r, c0 + i) for i < 32 into cv (zero outside the matrix), vectorised where the
-// row segment is contiguous and aligned.
-__device__ __forceinline__ void load_c32(const Epi &e, int64_t r, int64_t c0, int ncol, bool row_ok,
-                                         float *cv)
+// v[i] += beta * C(r, c0 + i) for i < ncol, vectorised where the row segment is
+// contiguous and aligned.
+__device__ __forceinline__ void add_c32(const Epi &e, int64_t r, int64_t c0, int ncol, float beta,
+                                        float *v)
 {
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-        cv[i] = 0.0f;
-    if (!row_ok || e.c_kind == C_NONE)
-        return;
     if (!e.c_trans) {
         const int64_t off = r * e.ldc + c0;
         if (ncol == 32 && (e.c_kind == C_BF16 || e.c_kind == C_PAIR) && (off & 7) == 0) {
             const uint4 *h = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(e.c0) + off);
+            const uint4 *l = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(e.c1) + off);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 uint4 u = __ldg(h + q);
-                const __nv_bfloat16 *b = reinterpret_cast<const __nv_bfloat16 *>(&u);
+                const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&u);
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    cv[q * 8 + j] = __bfloat162float(b[j]);
-            }
-            if (e.c_kind == C_PAIR) {
-                const uint4 *l = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(e.c1) + off);
+                for (int j = 0; j < 4; ++j) {
+                    float2 f = __bfloat1622float2(b[j]);
+                    v[q * 8 + 2 * j] += beta * f.x;
+                    v[q * 8 + 2 * j + 1] += beta * f.y;
+                }
+                if (e.c_kind == C_PAIR) {
+                    uint4 w = __ldg(l + q);
+                    const __nv_bfloat162 *d = reinterpret_cast<const __nv_bfloat162 *>(&w);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint4 u = __ldg(l + q);
-                    const __nv_bfloat16 *b = reinterpret_cast<const __nv_bfloat16 *>(&u);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        cv[q * 8 + j] += __bfloat162float(b[j]);
+                    for (int j = 0; j < 4; ++j) {
+                        float2 f = __bfloat1622float2(d[j]);
+                        v[q * 8 + 2 * j] += beta * f.x;
+                        v[q * 8 + 2 * j + 1] += beta * f.y;
+                    }
                 }
             }
             return;
@@ -288,10 +288,10 @@ __device__ __forceinline__ void load_c32(const Epi &e, int64_t r, int64_t c0, in
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 float4 u = __ldg(f + q);
-                cv[4 * q] = u.x;
-                cv[4 * q + 1] = u.y;
-                cv[4 * q + 2] = u.z;
-                cv[4 * q + 3] = u.w;
+                v[4 * q] += beta * u.x;
+                v[4 * q + 1] += beta * u.y;
+                v[4 * q + 2] += beta * u.z;
+                v[4 * q + 3] += beta * u.w;
             }
             return;
         }
@@ -310,11 +310,13 @@ __device__ __forceinline__ void load_c32(const Epi &e, int64_t r, int64_t c0, in
             if (e.c_kind == C_PAIR)
                 x += __bfloat162float(static_cast<const __nv_bfloat16 *>(e.c1)[off]);
         }
-        cv[i] = x;
+        v[i] += beta * x;
     }
 }
 
-constexpr int kStagePitch = 33;  // floats per staging row: conflict-free by rows and by columns
+// Fallback staging: 32 x 32 floats, element (a, b) at a * 32 + (b ^ a); rows and
+// columns are both free of bank conflicts.
+__device__ __forceinline__ int xs_idx(int a, int b) { return a * 32 + (b ^ a); }
 
 // Store a 32 x 32 block held in shared memory `st` (st[a][b] = value of tile
 // element (r0 + a, c0 + b)) to global memory, coalesced: warp lanes cover whole
@@ -344,7 +346,7 @@ __device__ __forceinline__ void store_block(const float *st, int kind, void *p0,
                 if (trans) { sa = b; sb = a; }
                 else if (symdiag && a > b) { sa = b; sb = a; }
                 else { sa = a; sb = b; }
-                x[j] = st[sa * kStagePitch + sb];
+                x[j] = st[xs_idx(sa, sb)];
             }
             if (R >= orows)
                 continue;
@@ -392,7 +394,7 @@ __device__ __forceinline__ void store_block(const float *st, int kind, void *p0,
                 if (trans) { sa = b; sb = a; }
                 else if (symdiag && a > b) { sa = b; sb = a; }
                 else { sa = a; sb = b; }
-                x[j] = st[sa * kStagePitch + sb];
+                x[j] = st[xs_idx(sa, sb)];
             }
             if (R >= orows)
                 continue;
@@ -428,7 +430,8 @@ __device__ __forceinline__ uint32_t stg_off_b16(int row, int col)
 // Stage the warp's 32 x 32 block (lane = block row, x[] = its 32 columns) and
 // store it with one or two TMA stores: at tile coordinates (x = c0, y = r0), or
 // transposed at (x = r0, y = c0). `kind` is O_F32, O_BF16 or O_PAIR (hi through
-// m0, lo through m1). stg0 / stg1 are 1024-byte aligned 4 KiB buffers of this warp.
+// m0, lo through m1). stg0 is this warp's 1024-byte aligned staging buffer (4 KiB
+// for FP32); for BF16 blocks stg0 and stg1 = stg0 + 2 KiB hold hi and lo.
 __device__ __forceinline__ void tma_store_block(const float *x, int kind, bool trans,
                                                 const CUtensorMap *m0, const CUtensorMap *m1,
                                                 int r0, int c0, uint8_t *stg0, uint8_t *stg1,
@@ -503,13 +506,16 @@ __device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiScal
     const bool row_ok = r < P.M;
     const int64_t rem = (int64_t)P.N - c0;
     const int ncol = rem < 32 ? (int)rem : 32;
-    float cv[32];
-    load_c32(e, r, c0, ncol, row_ok, cv);
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        v[i] *= s.alpha;
+    if (e.c_kind != C_NONE && row_ok)
+        add_c32(e, r, c0, ncol, s.beta, v);
     const bool diag_block = (r0 == c0);
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
         const int64_t c = c0 + i;
-        float x = s.alpha * v[i] + s.beta * cv[i];
+        float x = v[i];
         if (diag_block && r == c) {
             x += s.gamma;
             if (e.diag)
@@ -522,7 +528,8 @@ __device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiScal
         v[i] = x;
     }
     const bool symdiag = P.sym && diag_block;
-    uint8_t *stg0 = stg, *stg1 = stg + 4096;
+    // FP32 blocks use the whole 4 KiB; BF16 hi/lo blocks 2 KiB each.
+    uint8_t *stg0 = stg, *stg1 = stg + 2048;
     // Outputs through TMA stores (all but diagonal blocks of symmetric products).
     const bool o_tma = P.o_tma && e.o_kind != O_NONE && !symdiag;
     if (o_tma)
@@ -545,7 +552,7 @@ __device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiScal
     float *st = reinterpret_cast<float *>(stg);
 #pragma unroll
     for (int i = 0; i < 32; ++i)
-        st[lane * kStagePitch + i] = v[i];
+        st[xs_idx(lane, i)] = v[i];
     __syncwarp();
     if (e.o_kind != O_NONE && !o_tma)
         store_block(st, e.o_kind, e.o0, e.o1, e.ldo, r0, c0, P.M, P.N, e.o_trans != 0, symdiag, lane);
@@ -568,8 +575,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     constexpr int B_BYTES = BN * kBK * 2;
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * A_BYTES;
-    uint8_t *stage_all = sB + STAGES * B_BYTES;  // 4 epilogue warps x 8 KiB, 1024-aligned
-    uint64_t *full = reinterpret_cast<uint64_t *>(stage_all + 4 * 8192);
+    uint8_t *stage_all = sB + STAGES * B_BYTES;  // kEpiWarps x 4 KiB, 1024-aligned
+    uint64_t *full = reinterpret_cast<uint64_t *>(stage_all + kEpiWarps * 4096);
     uint64_t *empty = full + STAGES;
     uint64_t *tfull = empty + STAGES;
     uint64_t *tempty = tfull + 2;
@@ -589,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 128);
+            mbar_init(&tempty[b], 32 * kEpiWarps);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -703,7 +710,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue
         const int quad = warp & 3;  // TMEM lane quadrant this warp may access
-        uint8_t *stage_buf = stage_all + (warp - 2) * 8192;
+        const int half = (warp - 2) >> 2;  // two warps per quadrant split the column chunks
+        uint8_t *stage_buf = stage_all + (warp - 2) * 4096;
         int buf = 0;
         uint32_t tphase = 0;
         int last_prob = -1;
@@ -723,7 +731,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             const int64_t warp_row0 = (int64_t)tc.tm * kBM + quad * 32;
             double nrm = 0.0;
 #pragma unroll 1
-            for (int ch = 0; ch < BN / 32; ++ch) {
+            for (int ch = half; ch < BN / 32; ch += 2) {
                 const int64_t c0 = (int64_t)tc.tn * BN + ch * 32;
                 // Warp-uniform skips: chunk right of N, or wholly below the diagonal.
                 if (c0 >= P.N || warp_row0 >= P.M)
@@ -767,7 +775,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 template <int BN, int STAGES>
 constexpr int smem_bytes()
 {
-    return STAGES * (kBM + BN) * kBK * 2 + 4 * 8192 /* epilogue staging */ +
+    return STAGES * (kBM + BN) * kBK * 2 + kEpiWarps * 4096 /* epilogue staging */ +
            1024 /* alignment slack */ + 256 /* barriers */;
 }
 
