@@ -27,17 +27,19 @@ __device__ __forceinline__ void set_status(int *status, svt_status s)
 // Column norms (wide = 0): block (32, 8) covers 32 columns and kRowsPerBlock rows.
 constexpr int kRowsPerBlock = 256;
 
-__global__ void ingest_colnorm_kernel(const float *__restrict__ A, int64_t m, int64_t n,
-                                      int64_t lda, double *colnorm2, double *scal, int *status)
+// Block (bx, by) of the column-norm reduction; threads (tx, ty) in 32 x 8.
+__device__ __forceinline__ void colnorm_block(const float *__restrict__ A, int64_t m, int64_t n,
+                                              int64_t lda, double *colnorm2, double *scal,
+                                              int *status, int bx, int by, int tx, int ty)
 {
     __shared__ double part[8][33];
-    const int64_t col = (int64_t)blockIdx.x * 32 + threadIdx.x;
-    const int64_t r0 = (int64_t)blockIdx.y * kRowsPerBlock;
+    const int64_t col = (int64_t)bx * 32 + tx;
+    const int64_t r0 = (int64_t)by * kRowsPerBlock;
     const int64_t r1 = (m < r0 + kRowsPerBlock) ? m : r0 + kRowsPerBlock;
     double s = 0.0;
     bool finite = true;
     if (col < n) {
-        for (int64_t r = r0 + threadIdx.y; r < r1; r += 8) {
+        for (int64_t r = r0 + ty; r < r1; r += 8) {
             float a = A[r * lda + col];
             finite &= isfinite(a);
             s += (double)a * (double)a;
@@ -45,28 +47,37 @@ __global__ void ingest_colnorm_kernel(const float *__restrict__ A, int64_t m, in
     }
     if (!finite)
         set_status(status, SVT_ERR_NONFINITE);
-    part[threadIdx.y][threadIdx.x] = s;
+    part[ty][tx] = s;
     __syncthreads();
-    if (threadIdx.y == 0) {
+    if (ty == 0) {
         double t = 0.0;
         for (int i = 0; i < 8; ++i)
-            t += part[i][threadIdx.x];
+            t += part[i][tx];
         if (col < n)
             atomicAdd(&colnorm2[col], t);
         // block total for ||A||_F^2
         for (int o = 16; o > 0; o >>= 1)
             t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (threadIdx.x == 0)
+        if (tx == 0)
             atomicAdd(&scal[SC_NRM_A2], t);
     }
 }
 
-// Row norms (wide = 1): one warp per row.
-__global__ void ingest_rownorm_kernel(const float *__restrict__ A, int64_t m, int64_t n,
+__global__ void ingest_colnorm_kernel(const float *__restrict__ A, int64_t m, int64_t n,
                                       int64_t lda, double *colnorm2, double *scal, int *status)
 {
-    const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    const int lane = threadIdx.x & 31;
+    colnorm_block(A, m, n, lda, colnorm2, scal, status, blockIdx.x, blockIdx.y, threadIdx.x,
+                  threadIdx.y);
+}
+
+// Row norms (wide = 1): one warp per row.
+// Row norms of rows 8 bx .. 8 bx + 7 (one warp per row, 256 threads).
+__device__ __forceinline__ void rownorm_block(const float *__restrict__ A, int64_t m, int64_t n,
+                                              int64_t lda, double *colnorm2, double *scal,
+                                              int *status, int bx, int tid)
+{
+    const int64_t row = (int64_t)bx * 8 + tid / 32;
+    const int lane = tid & 31;
     if (row >= m)
         return;
     double s = 0.0;
@@ -86,6 +97,12 @@ __global__ void ingest_rownorm_kernel(const float *__restrict__ A, int64_t m, in
     }
 }
 
+__global__ void ingest_rownorm_kernel(const float *__restrict__ A, int64_t m, int64_t n,
+                                      int64_t lda, double *colnorm2, double *scal, int *status)
+{
+    rownorm_block(A, m, n, lda, colnorm2, scal, status, blockIdx.x, threadIdx.x);
+}
+
 // alpha = 2^e with e = round(log2 ||A||_F) (1 for a zero matrix): dividing by it is exact.
 __device__ __forceinline__ double pow2_alpha(double nrm2)
 {
@@ -100,25 +117,26 @@ __device__ __forceinline__ double pow2_alpha(double nrm2)
 
 // 32 x 32 tile of A -> same-orientation and transposed copies of A / alpha.
 template <bool F64>
-__global__ void ingest_split_kernel(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda,
-                                    float tau, void *xs_hi, void *xs_lo, int64_t ld_s, void *xt_hi,
-                                    void *xt_lo, int64_t ld_t, double *scal)
+__device__ __forceinline__ void split_block(const float *__restrict__ A, int64_t m, int64_t n,
+                                            int64_t lda, float tau, void *xs_hi, void *xs_lo,
+                                            int64_t ld_s, void *xt_hi, void *xt_lo, int64_t ld_t,
+                                            double *scal, int bx, int by, int tx, int ty)
 {
     __shared__ float tile[32][33];
     const double nrm2 = scal[SC_NRM_A2];
     const double alpha = pow2_alpha(nrm2);
     const float inv_alpha = (float)(1.0 / alpha);  // exact power of two
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    if (bx == 0 && by == 0 && tx == 0 && ty == 0) {
         scal[SC_ALPHA] = alpha;
         scal[SC_INV_ALPHA2] = 1.0 / (alpha * alpha);
         scal[SC_TAU2_SCALED] = ((double)tau * (double)tau) / (alpha * alpha);
         scal[SC_NRM_X0] = nrm2 / (alpha * alpha);
     }
-    const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
-    for (int k = threadIdx.y; k < 32; k += 8) {
-        const int64_t i = i0 + k, j = j0 + threadIdx.x;
+    const int64_t i0 = (int64_t)by * 32, j0 = (int64_t)bx * 32;
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t i = i0 + k, j = j0 + tx;
         float x = (i < m && j < n) ? A[i * lda + j] * inv_alpha : 0.0f;
-        tile[k][threadIdx.x] = x;
+        tile[k][tx] = x;
         if (i < m && j < n && xs_hi) {
             if (F64) {
                 static_cast<double *>(xs_hi)[i * ld_s + j] = (double)x;
@@ -132,10 +150,10 @@ __global__ void ingest_split_kernel(const float *__restrict__ A, int64_t m, int6
         }
     }
     __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += 8) {
-        const int64_t j = j0 + k, i = i0 + threadIdx.x;  // transposed element (j, i)
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t j = j0 + k, i = i0 + tx;  // transposed element (j, i)
         if (i < m && j < n && xt_hi) {
-            float x = tile[threadIdx.x][k];
+            float x = tile[tx][k];
             if (F64) {
                 static_cast<double *>(xt_hi)[j * ld_t + i] = (double)x;
             } else {
@@ -149,6 +167,15 @@ __global__ void ingest_split_kernel(const float *__restrict__ A, int64_t m, int6
     }
 }
 
+template <bool F64>
+__global__ void ingest_split_kernel(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda,
+                                    float tau, void *xs_hi, void *xs_lo, int64_t ld_s, void *xt_hi,
+                                    void *xt_lo, int64_t ld_t, double *scal)
+{
+    split_block<F64>(A, m, n, lda, tau, xs_hi, xs_lo, ld_s, xt_hi, xt_lo, ld_t, scal, blockIdx.x,
+                     blockIdx.y, threadIdx.x, threadIdx.y);
+}
+
 __global__ void finalize_kernel(double *scal, int *status, svt_status *user)
 {
     double nrm = scal[SC_NRM_OUT];
@@ -156,6 +183,71 @@ __global__ void finalize_kernel(double *scal, int *status, svt_status *user)
         atomicCAS(status, 0, (int)SVT_ERR_DIVERGED);
     if (user)
         *reinterpret_cast<int *>(user) = *status;
+}
+
+// ------------------------------------------------------------ grouped (batches)
+
+__device__ __forceinline__ int find_rec(const AuxRec *recs, int count, int b, bool split)
+{
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        int start = split ? recs[mid].blk_split : recs[mid].blk_reduce;
+        if (start <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void grouped_zero_kernel(const AuxRec *recs)
+{
+    const AuxRec &r = recs[blockIdx.x];
+    for (int64_t i = threadIdx.x; i < r.zero_words; i += blockDim.x)
+        reinterpret_cast<unsigned long long *>(r.scal)[i] = 0ull;
+}
+
+__global__ void grouped_reduce_kernel(const AuxRec *recs, const CallRec *calls, int count)
+{
+    const int i = find_rec(recs, count, blockIdx.x, false);
+    const AuxRec &r = recs[i];
+    const CallRec &c = calls[i];
+    const int lb = blockIdx.x - r.blk_reduce;
+    if (!r.wide) {
+        const int gx = (int)((r.n + 31) / 32);
+        colnorm_block(c.A, r.m, r.n, c.lda, r.colnorm, r.scal, r.status, lb % gx, lb / gx,
+                      threadIdx.x & 31, threadIdx.x >> 5);
+    } else {
+        rownorm_block(c.A, r.m, r.n, c.lda, r.colnorm, r.scal, r.status, lb, threadIdx.x);
+    }
+}
+
+__global__ void grouped_split_kernel(const AuxRec *recs, const CallRec *calls, int count)
+{
+    const int i = find_rec(recs, count, blockIdx.x, true);
+    const AuxRec &r = recs[i];
+    const CallRec &c = calls[i];
+    const int lb = blockIdx.x - r.blk_split;
+    const int gx = (int)((r.n + 31) / 32);
+    if (r.f64)
+        split_block<true>(c.A, r.m, r.n, c.lda, c.tau, r.xs_hi, nullptr, r.ld_s, r.xt_hi, nullptr,
+                          r.ld_t, r.scal, lb % gx, lb / gx, threadIdx.x & 31, threadIdx.x >> 5);
+    else
+        split_block<false>(c.A, r.m, r.n, c.lda, c.tau, r.xs_hi, r.xs_lo, r.ld_s, r.xt_hi, r.xt_lo,
+                           r.ld_t, r.scal, lb % gx, lb / gx, threadIdx.x & 31, threadIdx.x >> 5);
+}
+
+__global__ void grouped_finalize_kernel(const AuxRec *recs, const CallRec *calls, int count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count)
+        return;
+    const AuxRec &r = recs[i];
+    if (!isfinite(r.scal[SC_NRM_OUT]))
+        atomicCAS(r.status, 0, (int)SVT_ERR_DIVERGED);
+    if (calls[i].d_status)
+        *reinterpret_cast<int *>(calls[i].d_status) = *r.status;
 }
 
 // ------------------------------------------------------------ FP64 tier
@@ -292,6 +384,50 @@ cudaError_t ingest_split_launch(const float *A, int64_t m, int64_t n, int64_t ld
     else
         ingest_split_kernel<false><<<grid, dim3(32, 8), 0, s>>>(A, m, n, lda, tau, xs_hi, xs_lo,
                                                                  ld_s, xt_hi, xt_lo, ld_t, scal);
+    return cudaGetLastError();
+}
+
+int grouped_reduce_blocks(int64_t m, int64_t n, int wide)
+{
+    if (!wide)
+        return (int)(((n + 31) / 32) * ((m + kRowsPerBlock - 1) / kRowsPerBlock));
+    return (int)((m + 7) / 8);
+}
+
+int grouped_split_blocks(int64_t m, int64_t n) { return (int)(((n + 31) / 32) * ((m + 31) / 32)); }
+
+cudaError_t grouped_zero_launch(const AuxRec *recs, int count, cudaStream_t s)
+{
+    if (count <= 0)
+        return cudaSuccess;
+    grouped_zero_kernel<<<count, 256, 0, s>>>(recs);
+    return cudaGetLastError();
+}
+
+cudaError_t grouped_reduce_launch(const AuxRec *recs, const CallRec *calls, int count,
+                                  int blocks_reduce, cudaStream_t s)
+{
+    if (count <= 0 || blocks_reduce <= 0)
+        return cudaSuccess;
+    grouped_reduce_kernel<<<blocks_reduce, 256, 0, s>>>(recs, calls, count);
+    return cudaGetLastError();
+}
+
+cudaError_t grouped_split_launch(const AuxRec *recs, const CallRec *calls, int count,
+                                 int blocks_split, cudaStream_t s)
+{
+    if (count <= 0 || blocks_split <= 0)
+        return cudaSuccess;
+    grouped_split_kernel<<<blocks_split, 256, 0, s>>>(recs, calls, count);
+    return cudaGetLastError();
+}
+
+cudaError_t grouped_finalize_launch(const AuxRec *recs, const CallRec *calls, int count,
+                                    cudaStream_t s)
+{
+    if (count <= 0)
+        return cudaSuccess;
+    grouped_finalize_kernel<<<(count + 255) / 256, 256, 0, s>>>(recs, calls, count);
     return cudaGetLastError();
 }
 

@@ -195,6 +195,11 @@ struct TileCoord {
     bool valid;
 };
 
+__device__ __forceinline__ const TcProblem &prob_at(const TcLaunch &L, int p)
+{
+    return L.gtab ? L.gtab[p] : L.p[p];
+}
+
 // Linear tile index -> (problem, tile row, tile column).
 // Dense problems: column-major over the tile grid. Symmetric problems: only
 // tiles holding some element with row <= col; column tn holds r (tn + 1) row
@@ -203,11 +208,25 @@ template <int BN>
 __device__ TileCoord decode_tile(const TcLaunch &L, int t)
 {
     TileCoord tc{0, 0, 0, false};
-    int p = 0;
-    while (p + 1 < L.nprob && t >= L.tile_start[p + 1])
-        ++p;
-    const TcProblem &P = L.p[p];
-    int local = t - L.tile_start[p];
+    int p = 0, start = 0;
+    if (L.gtab) {
+        int lo = 0, hi = L.gcount - 1;  // last p with gstart[p] <= t
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (L.gstart[mid] <= t)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        p = lo;
+        start = L.gstart[p];
+    } else {
+        while (p + 1 < L.nprob && t >= L.tile_start[p + 1])
+            ++p;
+        start = L.tile_start[p];
+    }
+    const TcProblem &P = prob_at(L, p);
+    int local = t - start;
     tc.prob = p;
     if (!P.sym) {
         tc.tm = local % P.tiles_m;
@@ -234,13 +253,13 @@ struct EpiScales {
     float alpha, beta, gamma;
 };
 
-__device__ __forceinline__ EpiScales epi_scales(const Epi &e)
+__device__ __forceinline__ EpiScales epi_scales(const Epi &e, double alpha)
 {
-    EpiScales s{(float)e.alpha, (float)e.beta, (float)e.gamma};
+    EpiScales s{(float)alpha, (float)e.beta, (float)e.gamma};
     if (e.theta_src) {
         double theta = pow(*e.theta_src, e.theta_pow);
         if (theta > 0.0 && isfinite(theta)) {
-            s.alpha = (float)(e.alpha * pow(theta, -e.ea));
+            s.alpha = (float)(alpha * pow(theta, -e.ea));
             s.beta = (float)(e.beta * pow(theta, -e.eb));
             s.gamma = (float)(e.gamma * pow(theta, -e.eg));
         } else if (e.status) {
@@ -252,13 +271,13 @@ __device__ __forceinline__ EpiScales epi_scales(const Epi &e)
 
 // v[i] += beta * C(r, c0 + i) for i < ncol, vectorised where the row segment is
 // contiguous and aligned.
-__device__ __forceinline__ void add_c32(const Epi &e, int64_t r, int64_t c0, int ncol, float beta,
-                                        float *v)
+__device__ __forceinline__ void add_c32(const Epi &e, const void *cp0, int64_t ldc, int64_t r,
+                                        int64_t c0, int ncol, float beta, float *v)
 {
     if (!e.c_trans) {
-        const int64_t off = r * e.ldc + c0;
+        const int64_t off = r * ldc + c0;
         if (ncol == 32 && (e.c_kind == C_BF16 || e.c_kind == C_PAIR) && (off & 7) == 0) {
-            const uint4 *h = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(e.c0) + off);
+            const uint4 *h = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(cp0) + off);
             const uint4 *l = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(e.c1) + off);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -284,7 +303,7 @@ __device__ __forceinline__ void add_c32(const Epi &e, int64_t r, int64_t c0, int
             return;
         }
         if (ncol == 32 && e.c_kind == C_F32 && (off & 3) == 0) {
-            const float4 *f = reinterpret_cast<const float4 *>(static_cast<const float *>(e.c0) + off);
+            const float4 *f = reinterpret_cast<const float4 *>(static_cast<const float *>(cp0) + off);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 float4 u = __ldg(f + q);
@@ -301,12 +320,12 @@ __device__ __forceinline__ void add_c32(const Epi &e, int64_t r, int64_t c0, int
         if (i >= ncol)
             continue;
         const int64_t c = c0 + i;
-        const int64_t off = e.c_trans ? c * e.ldc + r : r * e.ldc + c;
+        const int64_t off = e.c_trans ? c * ldc + r : r * ldc + c;
         float x;
         if (e.c_kind == C_F32)
-            x = static_cast<const float *>(e.c0)[off];
+            x = static_cast<const float *>(cp0)[off];
         else {
-            x = __bfloat162float(static_cast<const __nv_bfloat16 *>(e.c0)[off]);
+            x = __bfloat162float(static_cast<const __nv_bfloat16 *>(cp0)[off]);
             if (e.c_kind == C_PAIR)
                 x += __bfloat162float(static_cast<const __nv_bfloat16 *>(e.c1)[off]);
         }
@@ -497,11 +516,22 @@ __device__ __forceinline__ void tma_store_block(const float *x, int kind, bool t
 // Values are computed in registers, staged in shared memory, then stored coalesced
 // to every requested destination: the output (row-major or transposed), the
 // extra transposed copy and, for symmetric products, the mirror.
-__device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiScales &s, int64_t r0,
-                                               int64_t c0, float *v, double &nrm, uint8_t *stg,
-                                               int lane)
+// Per-call fields of a grouped launch (C source, main output); the rest of the
+// epilogue comes from the problem.
+struct EpiOverride {
+    const void *c0;
+    int64_t ldc;
+    void *o0;
+    int64_t ldo;
+    int otma;
+};
+
+__device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiOverride &ov,
+                                               const EpiScales &s, int64_t r0, int64_t c0, float *v,
+                                               double &nrm, uint8_t *stg, int lane)
 {
     const Epi &e = P.ep;
+    const int p_otma = ov.otma;
     const int64_t r = r0 + lane;
     const bool row_ok = r < P.M;
     const int64_t rem = (int64_t)P.N - c0;
@@ -510,7 +540,7 @@ __device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiScal
     for (int i = 0; i < 32; ++i)
         v[i] *= s.alpha;
     if (e.c_kind != C_NONE && row_ok)
-        add_c32(e, r, c0, ncol, s.beta, v);
+        add_c32(e, ov.c0, ov.ldc, r, c0, ncol, s.beta, v);
     const bool diag_block = (r0 == c0);
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
@@ -531,17 +561,17 @@ __device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiScal
     // FP32 blocks use the whole 4 KiB; BF16 hi/lo blocks 2 KiB each.
     uint8_t *stg0 = stg, *stg1 = stg + 2048;
     // Outputs through TMA stores (all but diagonal blocks of symmetric products).
-    const bool o_tma = P.o_tma && e.o_kind != O_NONE && !symdiag;
+    const bool o_tma = p_otma && e.o_kind != O_NONE && !symdiag;
     if (o_tma)
         tma_store_block(v, e.o_kind, e.o_trans != 0, &P.mapO[0], &P.mapO[1], (int)r0, (int)c0,
                         stg0, stg1, lane);
-    if (P.sym && !diag_block && P.o_tma)  // mirror of a block strictly above the diagonal
+    if (P.sym && !diag_block && p_otma)  // mirror of a block strictly above the diagonal
         tma_store_block(v, e.o_kind, true, &P.mapO[0], &P.mapO[1], (int)r0, (int)c0, stg0, stg1,
                         lane);
     if (P.t_tma && e.t_kind != O_NONE)
         tma_store_block(v, e.t_kind, true, &P.mapT[0], &P.mapT[1], (int)r0, (int)c0, stg0, stg1,
                         lane);
-    const bool need_plain = (e.o_kind != O_NONE && !o_tma) || (P.sym && !diag_block && !P.o_tma) ||
+    const bool need_plain = (e.o_kind != O_NONE && !o_tma) || (P.sym && !diag_block && !p_otma) ||
                             (e.t_kind != O_NONE && !P.t_tma);
     if (!need_plain)
         return;
@@ -555,9 +585,9 @@ __device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiScal
         st[xs_idx(lane, i)] = v[i];
     __syncwarp();
     if (e.o_kind != O_NONE && !o_tma)
-        store_block(st, e.o_kind, e.o0, e.o1, e.ldo, r0, c0, P.M, P.N, e.o_trans != 0, symdiag, lane);
-    if (P.sym && !diag_block && !P.o_tma)
-        store_block(st, e.o_kind, e.o0, e.o1, e.ldo, r0, c0, P.M, P.N, true, false, lane);
+        store_block(st, e.o_kind, ov.o0, e.o1, ov.ldo, r0, c0, P.M, P.N, e.o_trans != 0, symdiag, lane);
+    if (P.sym && !diag_block && !p_otma)
+        store_block(st, e.o_kind, ov.o0, e.o1, ov.ldo, r0, c0, P.M, P.N, true, false, lane);
     if (e.t_kind != O_NONE && !P.t_tma)
         store_block(st, e.t_kind, e.t0, e.t1, e.ldt, r0, c0, P.M, P.N, true, false, lane);
     __syncwarp();
@@ -587,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    int *status0 = L.p[0].ep.status;
+    int *status0 = prob_at(L, 0).ep.status;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -614,7 +644,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const int total = *skip_flag ? 0 : L.tile_start[L.nprob];
+    const int total = *skip_flag ? 0 : (L.gtab ? L.gstart[L.gcount] : L.tile_start[L.nprob]);
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------ TMA producer
@@ -626,7 +656,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             TileCoord tc = decode_tile<BN>(L, t);
             if (!tc.valid)
                 continue;
-            const TcProblem &P = L.p[tc.prob];
+            const TcProblem &P = prob_at(L, tc.prob);
             const int kblocks = (P.K + kBK - 1) / kBK;
             for (int sg = 0; sg < P.nseg && ok; ++sg) {
                 const CUtensorMap *mL = &P.mapL[P.segL[sg]];
@@ -666,7 +696,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             TileCoord tc = decode_tile<BN>(L, t);
             if (!tc.valid)
                 continue;
-            const TcProblem &P = L.p[tc.prob];
+            const TcProblem &P = prob_at(L, tc.prob);
             const int kblocks = (P.K + kBK - 1) / kBK;
             if (!mbar_wait(&tempty[buf], tphase ^ 1u, abort_flag, status0, kWaitTimeoutNs))
                 break;
@@ -716,13 +746,34 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         uint32_t tphase = 0;
         int last_prob = -1;
         EpiScales sc{1.f, 0.f, 0.f};
+        EpiOverride ov{nullptr, 0, nullptr, 0, 0};
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
             TileCoord tc = decode_tile<BN>(L, t);
             if (!tc.valid)
                 continue;
-            const TcProblem &P = L.p[tc.prob];
+            const TcProblem &P = prob_at(L, tc.prob);
             if (tc.prob != last_prob) {
-                sc = epi_scales(P.ep);
+                ov.c0 = P.ep.c0;
+                ov.ldc = P.ep.ldc;
+                ov.o0 = P.ep.o0;
+                ov.ldo = P.ep.ldo;
+                ov.otma = P.o_tma;
+                double alpha = P.ep.alpha;
+                if (P.patch && L.calls) {  // grouped launch: per-call fields
+                    const CallRec &cr = L.calls[P.call_idx];
+                    if (P.patch & PT_C_IS_A) {
+                        ov.c0 = cr.A;
+                        ov.ldc = cr.lda;
+                    }
+                    if (P.patch & PT_O_IS_Y) {
+                        ov.o0 = cr.Y;
+                        ov.ldo = cr.ldy;
+                        ov.otma = 0;
+                    }
+                    if (P.patch & PT_ALPHA_NEG_TAU)
+                        alpha = -(double)cr.tau;
+                }
+                sc = epi_scales(P.ep, alpha);
                 last_prob = tc.prob;
             }
             if (!mbar_wait(&tfull[buf], tphase, abort_flag, status0, kWaitTimeoutNs))
@@ -740,7 +791,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                     continue;
                 float v[32];
                 tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + ch * 32), v);
-                epilogue_block(P, sc, warp_row0, c0, v, nrm, stage_buf, lane);
+                epilogue_block(P, ov, sc, warp_row0, c0, v, nrm, stage_buf, lane);
             }
             if (P.ep.norm_acc) {
 #pragma unroll
@@ -791,15 +842,44 @@ cudaError_t launch_bn(const TcLaunch &l, int num_sms, cudaStream_t s)
             return e;
         configured = true;
     }
-    int total = l.tile_start[l.nprob];
-    if (total <= 0)
+    int total = l.gtab ? -1 : l.tile_start[l.nprob];
+    if (total == 0)
         return cudaSuccess;
+    if (total < 0)
+        total = num_sms;  // grouped launch: the tile count lives on the device
     int grid = total < num_sms ? total : num_sms;
     tc_gemm_kernel<BN, STAGES><<<grid, kThreads, smem, s>>>(l);
     return cudaGetLastError();
 }
 
 } // namespace
+
+cudaError_t tc_gemm_launch_grouped(const TcLaunch &l, int bn, int total_tiles, int num_sms,
+                                   cudaStream_t s)
+{
+    if (total_tiles <= 0)
+        return cudaSuccess;
+    TcLaunch g = l;
+    g.nprob = 0;
+    if (bn == 256) {
+        constexpr int smem = smem_bytes<256, 4>();
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<256, 4>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess)
+            return e;
+        tc_gemm_kernel<256, 4><<<total_tiles < num_sms ? total_tiles : num_sms, kThreads, smem, s>>>(g);
+    } else if (bn == 128) {
+        constexpr int smem = smem_bytes<128, 6>();
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<128, 6>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess)
+            return e;
+        tc_gemm_kernel<128, 6><<<total_tiles < num_sms ? total_tiles : num_sms, kThreads, smem, s>>>(g);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 int tc_num_tiles(const TcProblem &p, int bn)
 {

@@ -58,7 +58,6 @@ Layout make_layout(int64_t m, int64_t n, const Resolved &r);
 // ------------------------------------------------------------ plan
 
 enum OpKind { OP_MEMSET, OP_REDUCE, OP_SPLIT, OP_TC, OP_F64, OP_PREP, OP_FINAL };
-enum Patch { PT_C_IS_A = 1, PT_O_IS_Y = 2, PT_ALPHA_NEG_TAU = 4 };
 
 struct Op {
     int kind;
@@ -88,6 +87,7 @@ struct Plan {
     std::vector<double> tc_flops;   // algorithmic flops of each tensor-core launch
     int tc_launches_per_solve = 0;
     int kernel_launches = 0;
+    int force_bn = 0;               // 0: tile width per launch; 128 / 256: fixed (grouped batches)
 };
 
 struct Key {
@@ -95,12 +95,13 @@ struct Key {
     int iters, prec, schedule, norm, polish, mode, hp_steps;
     double ell0, delta;
     size_t ws_base;
+    int force_bn;
     bool operator<(const Key &o) const
     {
         return std::tie(m, n, iters, prec, schedule, norm, polish, mode, hp_steps, ell0, delta,
-                        ws_base) < std::tie(o.m, o.n, o.iters, o.prec, o.schedule, o.norm,
-                                            o.polish, o.mode, o.hp_steps, o.ell0, o.delta,
-                                            o.ws_base);
+                        ws_base, force_bn) < std::tie(o.m, o.n, o.iters, o.prec, o.schedule,
+                                                      o.norm, o.polish, o.mode, o.hp_steps,
+                                                      o.ell0, o.delta, o.ws_base, o.force_bn);
     }
 };
 
@@ -141,7 +142,7 @@ struct svt_ctx {
 
 namespace svt {
 svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_t ws_base,
-                    size_t ws_avail, Plan **out);
+                    size_t ws_avail, Plan **out, int force_bn = 0);
 svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s);
 // Read the plan's internal status word back to host memory (async on s).
 svt_status plan_status_copy(svt_ctx *ctx, const Plan &P, int *host_dst, cudaStream_t s);

@@ -1,9 +1,15 @@
 // Batches and serving for libsvt (host code).
 //
-// svt_batch: every matrix gets its own plan at its own offset of the workspace;
-// the solves are issued round-robin over the context's worker streams, so the
-// independent matrices overlap on the device, and the caller's stream waits on
-// all of them.
+// svt_batch: every matrix gets its own plan at its own offset of the workspace.
+// When all matrices share one option set (the usual case), their solves are
+// merged stage by stage: each stage of every matrix -- both polar chains -- goes
+// out as ONE grouped persistent launch of the product kernel, whose problem table
+// (tensor maps included) lives in device memory, and the memory-bound steps run as
+// grouped kernels over all matrices. The whole launch sequence is captured once
+// per batch shape signature into a CUDA graph; a call uploads the per-matrix
+// pointers and thresholds (the call table) and replays the graph on the caller's
+// stream. Batches whose matrices differ in options fall back to per-matrix
+// solves spread over the context's worker streams.
 //
 // Serving: a scheduler thread owns an admission queue. Each tick it
 //   * retires requests whose completion event has fired (their workspace range
@@ -99,6 +105,62 @@ struct Request {
     svt_status result = SVT_OK;
 };
 
+// Grouped batch: the stage-merged launch sequence of `count` same-option solves.
+struct BatchPlan {
+    int count = 0;
+    size_t tables_off = 0;           // device tables, at this workspace offset
+    std::vector<TcLaunch> launches;  // grouped product launches (device pointers set)
+    std::vector<int> tiles, bns;
+    AuxRec *d_aux = nullptr;
+    CallRec *d_calls = nullptr;
+    int blocks_reduce = 0, blocks_split = 0;
+    CallRec *h_calls = nullptr;      // pinned staging of the call table
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t uploaded = nullptr;  // the previous replay consumed h_calls
+    bool pending = false;
+    int kernels_per_call = 0;
+    ~BatchPlan()
+    {
+        if (exec)
+            cudaGraphExecDestroy(exec);
+        if (uploaded)
+            cudaEventDestroy(uploaded);
+        if (h_calls)
+            cudaFreeHost(h_calls);
+    }
+};
+
+struct BatchKey {
+    std::vector<int64_t> shapes;     // m0, n0, m1, n1, ...
+    Resolved r;
+    bool operator<(const BatchKey &o) const
+    {
+        auto tie_r = [](const Resolved &x) {
+            return std::tie(x.iters, x.prec, x.schedule, x.norm, x.ell0, x.delta, x.polish, x.mode,
+                            x.hp_steps);
+        };
+        if (shapes != o.shapes)
+            return shapes < o.shapes;
+        return tie_r(r) < tie_r(o.r);
+    }
+};
+
+// Upper bound on the device table bytes of a grouped batch.
+size_t batch_table_bytes(int count, const Resolved &r)
+{
+    const size_t n_tc = 1 + 3 * (size_t)std::max(0, r.iters) + 2 + 1;
+    return align_up(sizeof(AuxRec) * count, kAlign) + align_up(sizeof(CallRec) * count, kAlign) +
+           n_tc * (align_up(sizeof(TcProblem) * 2 * count, kAlign) +
+                   align_up(sizeof(int) * (2 * count + 1), kAlign));
+}
+
+bool same_options(const Resolved &a, const Resolved &b)
+{
+    return a.iters == b.iters && a.prec == b.prec && a.schedule == b.schedule && a.norm == b.norm &&
+           a.ell0 == b.ell0 && a.delta == b.delta && a.polish == b.polish && a.mode == b.mode &&
+           a.hp_steps == b.hp_steps;
+}
+
 } // namespace
 
 struct ServeState {
@@ -117,6 +179,8 @@ struct ServeState {
     int *h_status = nullptr;  // pinned, one int per slot
     bool slot_used[kSlots] = {};
     int rr = 0;
+    std::map<BatchKey, std::unique_ptr<BatchPlan>> batches;
+    cudaStream_t capture = nullptr;
 };
 
 namespace svt {
@@ -228,6 +292,169 @@ void scheduler(svt_ctx *ctx, ServeState *s)
     }
 }
 
+// Merge the per-matrix plans stage by stage into grouped launches, upload the
+// device tables and capture the launch sequence in a CUDA graph.
+svt_status build_batch(svt_ctx *ctx, ServeState *s, const svt_matrix *mats, int count,
+                       const Resolved &r, const std::vector<size_t> &off, size_t tables_off,
+                       int bn, BatchPlan *bp)
+{
+    std::vector<Plan *> plans(count);
+    for (int i = 0; i < count; ++i) {
+        svt_status st = get_plan(ctx, mats[i].m, mats[i].n, r, off[i], ctx->ws_bytes - off[i],
+                                 &plans[i], bn);
+        if (st != SVT_OK)
+            return st;
+    }
+    // Structure check: same op kinds in the same order.
+    const Plan &p0 = *plans[0];
+    for (int i = 1; i < count; ++i) {
+        if (plans[i]->ops.size() != p0.ops.size())
+            return SVT_ERR_UNSUPPORTED;
+        for (size_t k = 0; k < p0.ops.size(); ++k)
+            if (plans[i]->ops[k].kind != p0.ops[k].kind)
+                return SVT_ERR_UNSUPPORTED;
+    }
+    for (const Op &op : p0.ops)
+        if (op.kind != OP_MEMSET && op.kind != OP_REDUCE && op.kind != OP_SPLIT &&
+            op.kind != OP_TC && op.kind != OP_FINAL)
+            return SVT_ERR_UNSUPPORTED;
+    bp->count = count;
+    bp->tables_off = tables_off;
+    uint8_t *tbase = ctx->ws + tables_off;
+    size_t toff = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = toff;
+        toff = align_up(toff + bytes, kAlign);
+        return o;
+    };
+    // Per-matrix records of the memory-bound steps.
+    std::vector<AuxRec> aux(count);
+    int blk_r = 0, blk_s = 0;
+    for (int i = 0; i < count; ++i) {
+        const Plan &P = *plans[i];
+        const Layout &L = P.lay;
+        uint8_t *base = ctx->ws + P.ws_base;
+        AuxRec &a = aux[i];
+        std::memset(&a, 0, sizeof(a));
+        a.m = P.m;
+        a.n = P.n;
+        a.wide = P.wide ? 1 : 0;
+        a.f64 = (r.prec == SVT_FP64) ? 1 : 0;
+        a.scal = reinterpret_cast<double *>(base + L.scal);
+        a.status = reinterpret_cast<int *>(base + L.status);
+        a.colnorm = reinterpret_cast<double *>(base + L.colnorm);
+        a.zero_words = (int64_t)((L.colnorm + (size_t)L.N * sizeof(double) - L.scal) / 8);
+        const Buf &same = P.wide ? L.Xt[0] : L.X[0];
+        const Buf &tran = P.wide ? L.X[0] : L.Xt[0];
+        a.xs_hi = base + same.hi;
+        a.xs_lo = same.has_lo ? base + same.lo : nullptr;
+        a.ld_s = same.ld;
+        a.xt_hi = base + tran.hi;
+        a.xt_lo = tran.has_lo ? base + tran.lo : nullptr;
+        a.ld_t = tran.ld;
+        if (r.prec == SVT_BF16) {  // lo part of X0^T only, for the Gram
+            if (P.wide)
+                a.xs_lo = base + L.XtLo0.hi;
+            else
+                a.xt_lo = base + L.XtLo0.hi;
+        }
+        a.blk_reduce = blk_r;
+        a.blk_split = blk_s;
+        blk_r += grouped_reduce_blocks(P.m, P.n, a.wide);
+        blk_s += grouped_split_blocks(P.m, P.n);
+    }
+    bp->blocks_reduce = blk_r;
+    bp->blocks_split = blk_s;
+    bp->d_aux = reinterpret_cast<AuxRec *>(tbase + take(sizeof(AuxRec) * count));
+    bp->d_calls = reinterpret_cast<CallRec *>(tbase + take(sizeof(CallRec) * count));
+    if (cudaMemcpy(bp->d_aux, aux.data(), sizeof(AuxRec) * count, cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return SVT_ERR_CUDA;
+    // Grouped product launches: op k of every matrix.
+    std::vector<TcProblem> probs;
+    std::vector<int> starts;
+    for (size_t k = 0; k < p0.ops.size(); ++k) {
+        if (p0.ops[k].kind != OP_TC)
+            continue;
+        probs.clear();
+        starts.clear();
+        int total = 0;
+        for (int i = 0; i < count; ++i) {
+            const Plan &P = *plans[i];
+            const int li = P.ops[k].idx;
+            const TcLaunch &l = P.tc[li];
+            for (int q = 0; q < l.nprob; ++q) {
+                TcProblem tp = l.p[q];
+                tp.patch = 0;
+                for (const PatchRec &pr : P.patches)
+                    if (pr.kind == OP_TC && pr.launch == li && pr.prob == q)
+                        tp.patch |= pr.flags;
+                tp.call_idx = i;
+                if (tp.patch & PT_O_IS_Y)
+                    tp.o_tma = 0;  // per-call output: plain stores
+                starts.push_back(total);
+                total += tc_num_tiles(tp, bn);
+                probs.push_back(tp);
+            }
+        }
+        starts.push_back(total);
+        TcProblem *dp = reinterpret_cast<TcProblem *>(tbase + take(sizeof(TcProblem) * probs.size()));
+        int *ds = reinterpret_cast<int *>(tbase + take(sizeof(int) * starts.size()));
+        if (toff > batch_table_bytes(count, r))
+            return SVT_ERR_OOM;
+        if (cudaMemcpy(dp, probs.data(), sizeof(TcProblem) * probs.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(ds, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+            return SVT_ERR_CUDA;
+        TcLaunch L;
+        std::memset(&L, 0, sizeof(L));
+        L.gtab = dp;
+        L.gstart = ds;
+        L.gcount = (int)probs.size();
+        L.calls = bp->d_calls;
+        bp->launches.push_back(L);
+        bp->tiles.push_back(total);
+        bp->bns.push_back(bn);
+    }
+    if (cudaMallocHost(reinterpret_cast<void **>(&bp->h_calls), sizeof(CallRec) * count) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&bp->uploaded, cudaEventDisableTiming) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    // Capture: calls upload, zero, reduce, split, grouped products, finalize.
+    if (!s->capture && cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    for (size_t k = 0; k < bp->launches.size(); ++k)  // set function attributes before capture
+        if (tc_gemm_launch_grouped(bp->launches[k], bp->bns[k], 0, ctx->num_sms, s->capture) !=
+            cudaSuccess)
+            return SVT_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cs = s->capture;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    bool ok = cudaMemcpyAsync(bp->d_calls, bp->h_calls, sizeof(CallRec) * count,
+                              cudaMemcpyHostToDevice, cs) == cudaSuccess;
+    ok = ok && grouped_zero_launch(bp->d_aux, count, cs) == cudaSuccess;
+    ok = ok && grouped_reduce_launch(bp->d_aux, bp->d_calls, count, bp->blocks_reduce, cs) == cudaSuccess;
+    ok = ok && grouped_split_launch(bp->d_aux, bp->d_calls, count, bp->blocks_split, cs) == cudaSuccess;
+    for (size_t k = 0; ok && k < bp->launches.size(); ++k)
+        ok = tc_gemm_launch_grouped(bp->launches[k], bp->bns[k], bp->tiles[k], ctx->num_sms, cs) ==
+             cudaSuccess;
+    ok = ok && grouped_finalize_launch(bp->d_aux, bp->d_calls, count, cs) == cudaSuccess;
+    cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    if (!ok || ec != cudaSuccess || !graph) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return SVT_ERR_CUDA;
+    }
+    cudaError_t ei = cudaGraphInstantiate(&bp->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess)
+        return SVT_ERR_CUDA;
+    bp->kernels_per_call = 4 + (int)bp->launches.size();
+    return SVT_OK;
+}
+
 } // namespace
 
 void serve_shutdown(svt_ctx *ctx)
@@ -252,6 +479,9 @@ void serve_shutdown(svt_ctx *ctx)
             cudaEventDestroy(s->events[i]);
     if (s->h_status)
         cudaFreeHost(s->h_status);
+    s->batches.clear();
+    if (s->capture)
+        cudaStreamDestroy(s->capture);
     for (auto &kv : s->tickets)
         delete kv.second;
     for (Request *r : s->queue)
@@ -272,20 +502,61 @@ bool serve_busy(svt_ctx *ctx)
 
 } // namespace svt
 
+namespace {
+
+// Tile width of a grouped batch: the one with less padded tensor work over the
+// matrices' largest products (M x N), 128-wide tiles weighted as ~15 % less
+// efficient per flop.
+int batch_bn(const svt_matrix *mats, int count)
+{
+    double a128 = 0, a256 = 0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t M = std::max(mats[i].m, mats[i].n), N = std::min(mats[i].m, mats[i].n);
+        const double tm = (double)((M + kBM - 1) / kBM);
+        a128 += tm * (double)((N + 127) / 128) * 128.0 / 0.85;
+        a256 += tm * (double)((N + 255) / 256) * 256.0;
+    }
+    return a128 < a256 ? 128 : 256;
+}
+
+// Options of all matrices resolved; returns false on an invalid option set.
+bool resolve_all(const svt_matrix *mats, int count, std::vector<Resolved> &res, bool *same)
+{
+    res.resize(count);
+    *same = true;
+    for (int i = 0; i < count; ++i) {
+        if (!resolve(&mats[i].opt, &res[i]))
+            return false;
+        if (i > 0 && !same_options(res[i], res[0]))
+            *same = false;
+    }
+    if (count > 0 && res[0].prec == SVT_FP64)
+        *same = false;  // the FP64 tier runs per-matrix launches
+    if (count > 0 && (!res[0].polish || res[0].mode != SVT_MODE_SVT))
+        *same = false;  // grouped kernels cover the default pipeline
+    return true;
+}
+
+} // namespace
+
 extern "C" {
 
 svt_status svt_batch_workspace_bytes(const svt_matrix *mats, int count, size_t *out)
 {
     if (!out || count < 0 || (count > 0 && !mats))
         return SVT_ERR_INVALID;
+    std::vector<Resolved> res;
+    bool same = false;
+    if (!resolve_all(mats, count, res, &same))
+        return SVT_ERR_INVALID;
     size_t total = 0;
     for (int i = 0; i < count; ++i) {
-        size_t b = 0;
-        svt_status st = svt_workspace_bytes_ex(mats[i].m, mats[i].n, &mats[i].opt, &b);
-        if (st != SVT_OK)
-            return st;
-        total += align_up(b, kAlign);
+        if (mats[i].m <= 0 || mats[i].n <= 0)
+            return SVT_ERR_INVALID;
+        total += align_up(make_layout(mats[i].m, mats[i].n, res[i]).total, kAlign);
     }
+    if (same && count > 0)
+        total += batch_table_bytes(count, res[0]);
     *out = total;
     return SVT_OK;
 }
@@ -294,9 +565,14 @@ svt_status svt_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, void *str
 {
     if (!ctx || count < 0 || (count > 0 && !mats))
         return SVT_ERR_INVALID;
+    if (count == 0)
+        return SVT_OK;
     if (serve_busy(ctx))
         return SVT_ERR_BUSY;
-    std::vector<Resolved> res(count);
+    std::vector<Resolved> res;
+    bool same = false;
+    if (!resolve_all(mats, count, res, &same))
+        return SVT_ERR_INVALID;
     size_t total = 0;
     std::vector<size_t> off(count);
     for (int i = 0; i < count; ++i) {
@@ -304,8 +580,6 @@ svt_status svt_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, void *str
         svt_status st = validate(m.A, m.m, m.n, m.lda, m.tau, m.Y, m.ldy);
         if (st != SVT_OK)
             return st;
-        if (!resolve(&m.opt, &res[i]))
-            return SVT_ERR_INVALID;
         if (res[i].prec == SVT_FP64 && (m.m > kF64MaxDim || m.n > kF64MaxDim))
             return SVT_ERR_UNSUPPORTED;
         off[i] = total;
@@ -318,7 +592,55 @@ svt_status svt_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, void *str
         return SVT_ERR_CUDA;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     std::lock_guard<std::mutex> g(ctx->mu);
-    // Worker streams start after everything already queued on the caller's stream.
+
+    // Grouped path: one launch per stage for all matrices, replayed from a CUDA graph.
+    if (same && total + batch_table_bytes(count, res[0]) <= ctx->ws_bytes) {
+        BatchKey key;
+        key.r = res[0];
+        for (int i = 0; i < count; ++i) {
+            key.shapes.push_back(mats[i].m);
+            key.shapes.push_back(mats[i].n);
+        }
+        BatchPlan *bp = nullptr;
+        auto it = s->batches.find(key);
+        if (it != s->batches.end()) {
+            bp = it->second.get();
+        } else {
+            if (s->batches.size() > 16)
+                s->batches.clear();
+            auto nb = std::make_unique<BatchPlan>();
+            svt_status st = build_batch(ctx, s, mats, count, res[0], off, total, batch_bn(mats, count),
+                                        nb.get());
+            if (st == SVT_OK) {
+                bp = nb.get();
+                s->batches[key] = std::move(nb);
+            } else if (st != SVT_ERR_UNSUPPORTED) {
+                return st;
+            }
+        }
+        if (bp) {
+            if (bp->pending && cudaEventSynchronize(bp->uploaded) != cudaSuccess)
+                return SVT_ERR_CUDA;
+            for (int i = 0; i < count; ++i) {
+                CallRec &c = bp->h_calls[i];
+                c.A = mats[i].A;
+                c.Y = mats[i].Y;
+                c.lda = mats[i].lda;
+                c.ldy = mats[i].ldy;
+                c.tau = mats[i].tau;
+                c.pad = 0;
+                c.d_status = mats[i].d_status;
+            }
+            if (cudaGraphLaunch(bp->exec, cs) != cudaSuccess ||
+                cudaEventRecord(bp->uploaded, cs) != cudaSuccess)
+                return SVT_ERR_CUDA;
+            bp->pending = true;
+            ctx->launches += (uint64_t)bp->kernels_per_call;
+            return SVT_OK;
+        }
+    }
+
+    // Per-matrix solves over the worker streams (mixed options, FP64 tier).
     cudaEvent_t ev = s->events[0];
     if (cudaEventRecord(ev, cs) != cudaSuccess)
         return SVT_ERR_CUDA;
@@ -336,7 +658,6 @@ svt_status svt_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, void *str
         if (st != SVT_OK)
             return st;
     }
-    // The caller's stream waits for all worker streams.
     for (int i = 0; i < kStreams; ++i) {
         if (cudaEventRecord(s->events[1 + i], s->streams[i]) != cudaSuccess ||
             cudaStreamWaitEvent(cs, s->events[1 + i], 0) != cudaSuccess)

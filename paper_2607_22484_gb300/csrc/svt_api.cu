@@ -354,6 +354,8 @@ struct Builder {
         for (const Prod &q : prods)
             if (q.N > 128)
                 bn = 256;
+        if (plan->force_bn)
+            bn = plan->force_bn;
         TcLaunch l;
         std::memset(&l, 0, sizeof(l));
         l.nprob = (int)prods.size();
@@ -785,10 +787,10 @@ svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s)
 }
 
 svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_t ws_base,
-                    size_t ws_avail, Plan **out)
+                    size_t ws_avail, Plan **out, int force_bn)
 {
     Key k{m, n, r.iters, r.prec, r.schedule, r.norm, r.polish, r.mode, r.hp_steps, r.ell0, r.delta,
-          ws_base};
+          ws_base, force_bn};
     auto it = ctx->plans.find(k);
     if (it != ctx->plans.end()) {
         *out = it->second.get();
@@ -801,6 +803,7 @@ svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_
     plan->opt = r;
     plan->lay = make_layout(m, n, r);
     plan->ws_base = ws_base;
+    plan->force_bn = force_bn;
     if (plan->lay.total > ws_avail)
         return SVT_ERR_OOM;
     plan->coef.assign((size_t)std::max(1, 3 * r.iters), 0.0);

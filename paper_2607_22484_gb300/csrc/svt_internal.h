@@ -61,6 +61,20 @@ struct Epi {
     int *status;                     // device status word of the solve
 };
 
+// Per-call arguments of one matrix, read by the kernels of a grouped launch
+// (device table, uploaded per call).
+struct CallRec {
+    const float *A;
+    float *Y;
+    int64_t lda, ldy;
+    float tau;
+    int pad;
+    svt_status *d_status;
+};
+
+// Problem fields that come from the call table in grouped launches.
+enum Patch { PT_C_IS_A = 1, PT_O_IS_Y = 2, PT_ALPHA_NEG_TAU = 4 };
+
 // One product of a grouped tensor-core launch.
 struct TcProblem {
     CUtensorMap mapL[2];             // L operands, box 64 x 128
@@ -68,6 +82,7 @@ struct TcProblem {
     CUtensorMap mapO[2];             // output hi/lo (or FP32), box 32 x 32, for TMA stores
     CUtensorMap mapT[2];             // transposed copy hi/lo, box 32 x 32
     int o_tma, t_tma;                // 1: store through mapO / mapT
+    int patch, call_idx;             // grouped launches: fields taken from calls[call_idx]
     int nseg;
     int segL[3], segR[3];
     int M, N, K;
@@ -80,6 +95,11 @@ struct TcLaunch {
     int nprob;
     int tile_start[kMaxProblems + 1];
     TcProblem p[kMaxProblems];
+    // Grouped launches: problems and tile prefix sums in device memory instead.
+    const TcProblem *gtab;
+    const int *gstart;               // gcount + 1 entries
+    int gcount;
+    const CallRec *calls;
 };
 
 // One product of the FP64 SIMT path: D = L R^T, L M x K (ldl), R N x K (ldr).
@@ -99,6 +119,10 @@ struct F64Launch {
 // ---- launchers (defined in the .cu files) ----
 int tc_num_tiles(const TcProblem &p, int bn);
 cudaError_t tc_gemm_launch(const TcLaunch &l, int bn, int num_sms, cudaStream_t s);
+// Grouped launch: l.gtab / l.gstart / l.gcount / l.calls point to device memory;
+// total_tiles (host copy of gstart[gcount]) sizes the grid.
+cudaError_t tc_gemm_launch_grouped(const TcLaunch &l, int bn, int total_tiles, int num_sms,
+                                   cudaStream_t s);
 cudaError_t f64_gemm_launch(const F64Launch &l, cudaStream_t s);
 
 // Ingest: FP64 column norms of the tall matrix and ||A||_F^2.
@@ -119,6 +143,34 @@ cudaError_t ingest_split_launch(const float *A, int64_t m, int64_t n, int64_t ld
 // Final status: non-finite output norm -> DIVERGED (unless already set), then
 // copy the internal status word to the caller's (if any).
 cudaError_t finalize_launch(double *scal, int *status, svt_status *user_status, cudaStream_t s);
+
+// Per-matrix record of the grouped memory-bound kernels (device table).
+struct AuxRec {
+    int64_t m, n;                    // input shape
+    int wide, f64;
+    double *scal;                    // scalar slots; scal .. scal + zero_words are cleared
+    int *status;
+    double *colnorm;
+    int64_t zero_words;              // 8-byte words from scal to the end of colnorm
+    void *xs_hi, *xs_lo;             // same-orientation copy of X0 (hi, lo)
+    int64_t ld_s;
+    void *xt_hi, *xt_lo;             // transposed copy
+    int64_t ld_t;
+    int blk_reduce, blk_split;       // first block of this matrix in the grouped grids
+};
+
+// Grouped memory-bound kernels over `count` matrices (records and call table in
+// device memory; blocks_* = total blocks, i.e. the last record's start + its blocks).
+cudaError_t grouped_zero_launch(const AuxRec *recs, int count, cudaStream_t s);
+cudaError_t grouped_reduce_launch(const AuxRec *recs, const CallRec *calls, int count,
+                                  int blocks_reduce, cudaStream_t s);
+cudaError_t grouped_split_launch(const AuxRec *recs, const CallRec *calls, int count,
+                                 int blocks_split, cudaStream_t s);
+cudaError_t grouped_finalize_launch(const AuxRec *recs, const CallRec *calls, int count,
+                                    cudaStream_t s);
+// Blocks the grouped reduce / split kernels use for one m x n matrix.
+int grouped_reduce_blocks(int64_t m, int64_t n, int wide);
+int grouped_split_blocks(int64_t m, int64_t n);
 
 // Host schedule (schedule.cpp).
 // coef[3t..3t+2] = (a_t, b_t, c_t); lo_out (nullable) receives the lower end l_t of

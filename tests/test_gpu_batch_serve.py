@@ -121,3 +121,31 @@ def test_serving_rejects_oversized_and_invalid():
     with pytest.raises(pkg.SVTError) as e:
         ctx.submit(a, -0.5, y)
     assert e.value.status == pkg.binding.ERR_INVALID
+
+
+def test_batch_graph_replay_new_data_and_mixed_fallback():
+    """Same shape signature twice (the captured graph is replayed with a new call
+    table), then a batch with mixed options (per-matrix fallback path)."""
+    items = _items(8, seed=47)
+    ctx = pkg.Context(0, workspace_bytes=1 << 20)
+    for rep in range(2):
+        mats = [it.matrix() * (1.0 + 0.5 * rep) for it in items]
+        taus = [it.tau * (1.0 + 0.5 * rep) for it in items]
+        As = [torch.from_numpy(m.astype(np.float32)).cuda() for m in mats]
+        outs = ctx.batch(As, taus, opts={"iters": 20, "prec": "bf16"})
+        torch.cuda.synchronize()
+        for m, tau, y in zip(mats, taus, outs):
+            exact, (u, s, v) = oracle.svt_definition(m.astype(np.float32).astype(np.float64), tau,
+                                                     return_svd=True)
+            if oracle.gap(s, tau) >= 0.05:
+                assert oracle.relerr(y.cpu().numpy(), exact) < 2e-2
+    As = [torch.from_numpy(it.matrix()).cuda() for it in items[:4]]
+    opts = [{"iters": 20, "prec": "bf16"}, {"iters": 20, "prec": "fp32"},
+            {"iters": 30, "prec": "fp32", "schedule": "ns3"}, {"iters": 20, "prec": "bf16"}]
+    outs = ctx.batch(As, [it.tau for it in items[:4]], opts=opts)
+    torch.cuda.synchronize()
+    for it, y, o in zip(items[:4], outs, opts):
+        exact, (u, s, v) = oracle.svt_definition(it.matrix().astype(np.float64), it.tau,
+                                                 return_svd=True)
+        if oracle.gap(s, it.tau) >= 0.05:
+            assert oracle.relerr(y.cpu().numpy(), exact) < (2e-2 if o["prec"] == "bf16" else 1e-4)
