@@ -144,6 +144,9 @@ namespace svt {
 svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_t ws_base,
                     size_t ws_avail, Plan **out, int force_bn = 0);
 svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s);
+// Ops [first, last) of a plan only (the serving loop advances requests op by op).
+svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, size_t first,
+                   size_t last);
 // Read the plan's internal status word back to host memory (async on s).
 svt_status plan_status_copy(svt_ctx *ctx, const Plan &P, int *host_dst, cudaStream_t s);
 void serve_shutdown(svt_ctx *ctx);

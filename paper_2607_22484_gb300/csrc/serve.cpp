@@ -11,14 +11,18 @@
 // stream. Batches whose matrices differ in options fall back to per-matrix
 // solves spread over the context's worker streams.
 //
-// Serving: a scheduler thread owns an admission queue. Each tick it
-//   * retires requests whose completion event has fired (their workspace range
-//     goes back to the arena, their status is read from the pinned copy),
+// Serving (continuous batching at stage granularity): a scheduler thread owns an
+// admission queue. Each tick it
+//   * retires requests whose last op has completed (their workspace range goes
+//     back to the arena, their status is read from the pinned copy),
 //   * admits queued requests in arrival order while a slot is free and their
 //     workspace fits in a free range of the context's workspace (first fit),
-//     and enqueues each admitted request's whole solve on a worker stream.
-// Requests that arrive while others run are admitted as soon as slots and
-// memory free up, and their kernels overlap with the running ones.
+//   * issues one window on its stream: grouped ingest of the newly admitted,
+//     ONE grouped product launch per tile width that carries the next stage of
+//     every active request (both polar chains of each), and grouped finalize of
+//     requests at their last op.
+// A request therefore joins the very next window after memory frees up, and
+// its stages share launches with whatever else is running.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -101,9 +105,18 @@ struct Request {
     size_t ws_len = 0, ws_off = 0;
     int slot = -1;
     double t_submit = 0, t_done = 0;
-    int state = 0;  // 0 queued, 1 running, 2 done
+    int state = 0;  // 0 queued, 1 running (ops being issued), 3 all issued, 2 done
     svt_status result = SVT_OK;
+    Plan *plan = nullptr;
+    size_t pc = 0;          // next op of the plan to issue
+    bool grouped = false;   // ops limited to the kinds the grouped kernels cover
 };
+
+// Device tables of one serving window live in a ring of slots at the end of the
+// workspace; each slot is staged from its own pinned host buffer.
+constexpr int kRing = 8;
+constexpr size_t kRingSlotBytes = 128 << 10;
+constexpr size_t kRingBytes = kRing * kRingSlotBytes;
 
 // Grouped batch: the stage-merged launch sequence of `count` same-option solves.
 struct BatchPlan {
@@ -181,6 +194,13 @@ struct ServeState {
     int rr = 0;
     std::map<BatchKey, std::unique_ptr<BatchPlan>> batches;
     cudaStream_t capture = nullptr;
+    // windowed serving
+    cudaStream_t win = nullptr;       // all windows are issued in order on this stream
+    uint8_t *h_ring = nullptr;        // pinned, kRing x kRingSlotBytes
+    cudaEvent_t ring_ev[kRing] = {};  // slot k's window has been consumed
+    bool ring_busy[kRing] = {};
+    int ring_next = 0;
+    uint64_t windows = 0;
 };
 
 namespace svt {
@@ -199,6 +219,13 @@ svt_status start_workers(svt_ctx *ctx, ServeState *s)
             return SVT_ERR_CUDA;
     if (!s->h_status && cudaMallocHost(reinterpret_cast<void **>(&s->h_status), sizeof(int) * kSlots) != cudaSuccess)
         return SVT_ERR_CUDA;
+    if (!s->win && cudaStreamCreateWithFlags(&s->win, cudaStreamNonBlocking) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    if (!s->h_ring && cudaMallocHost(reinterpret_cast<void **>(&s->h_ring), kRingBytes) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    for (int i = 0; i < kRing; ++i)
+        if (!s->ring_ev[i] && cudaEventCreateWithFlags(&s->ring_ev[i], cudaEventDisableTiming) != cudaSuccess)
+            return SVT_ERR_CUDA;
     return SVT_OK;
 }
 
@@ -209,27 +236,265 @@ ServeState *state_of(svt_ctx *ctx)
     return ctx->serve;
 }
 
+bool grouped_kinds(const Plan &P)
+{
+    for (const Op &op : P.ops)
+        if (op.kind != OP_MEMSET && op.kind != OP_REDUCE && op.kind != OP_SPLIT &&
+            op.kind != OP_TC && op.kind != OP_FINAL)
+            return false;
+    return true;
+}
+
+void finish(ServeState *s, Request *r, svt_status st)
+{
+    r->result = st;
+    r->state = 2;
+    r->t_done = now_ms();
+    s->arena.release(r->ws_off, r->ws_len);
+    s->slot_used[r->slot] = false;
+}
+
+// One serving window: grouped ingest of newly admitted requests, one grouped
+// product launch per tile width holding the next product stage of every active
+// request, grouped finalize of requests that reached their last op.
+svt_status issue_window(svt_ctx *ctx, ServeState *s)
+{
+    // Ring slot for this window's tables.
+    const int k = s->ring_next;
+    if (s->ring_busy[k]) {
+        cudaError_t q = cudaEventQuery(s->ring_ev[k]);
+        if (q == cudaErrorNotReady)
+            return SVT_ERR_NOT_READY;  // the device is a full ring behind: try next tick
+        if (q != cudaSuccess)
+            return SVT_ERR_CUDA;
+        s->ring_busy[k] = false;
+    }
+    uint8_t *h = s->h_ring + (size_t)k * kRingSlotBytes;
+    uint8_t *d = ctx->ws + (ctx->ws_bytes - kRingBytes) + (size_t)k * kRingSlotBytes;
+    size_t used = 0;
+    auto take = [&](size_t bytes) -> size_t {
+        size_t o = used;
+        used = align_up(used + bytes, kAlign);
+        return o;
+    };
+    std::vector<Request *> ingest, tc, fin, single;
+    for (Request *r : s->active) {
+        if (r->state != 1)
+            continue;
+        if (!r->grouped) {
+            single.push_back(r);
+            continue;
+        }
+        const Op &op = r->plan->ops[r->pc];
+        if (op.kind == OP_MEMSET)
+            ingest.push_back(r);
+    }
+    // Ingest: MEMSET, REDUCE, SPLIT are the first three ops of a grouped plan.
+    std::vector<AuxRec> aux;
+    std::vector<CallRec> calls;
+    auto call_of = [](const Request *r) {
+        CallRec c;
+        c.A = r->m.A;
+        c.Y = r->m.Y;
+        c.lda = r->m.lda;
+        c.ldy = r->m.ldy;
+        c.tau = r->m.tau;
+        c.pad = 0;
+        c.d_status = r->m.d_status;
+        return c;
+    };
+    auto aux_of = [&](const Request *r, int br, int bs) {
+        const Plan &P = *r->plan;
+        const Layout &L = P.lay;
+        uint8_t *base = ctx->ws + P.ws_base;
+        AuxRec a;
+        std::memset(&a, 0, sizeof(a));
+        a.m = P.m;
+        a.n = P.n;
+        a.wide = P.wide ? 1 : 0;
+        a.scal = reinterpret_cast<double *>(base + L.scal);
+        a.status = reinterpret_cast<int *>(base + L.status);
+        a.colnorm = reinterpret_cast<double *>(base + L.colnorm);
+        a.zero_words = (int64_t)((L.colnorm + (size_t)L.N * sizeof(double) - L.scal) / 8);
+        const Buf &same = P.wide ? L.Xt[0] : L.X[0];
+        const Buf &tran = P.wide ? L.X[0] : L.Xt[0];
+        a.xs_hi = base + same.hi;
+        a.xs_lo = same.has_lo ? base + same.lo : nullptr;
+        a.ld_s = same.ld;
+        a.xt_hi = base + tran.hi;
+        a.xt_lo = tran.has_lo ? base + tran.lo : nullptr;
+        a.ld_t = tran.ld;
+        if (P.opt.prec == SVT_BF16) {
+            if (P.wide)
+                a.xs_lo = base + L.XtLo0.hi;
+            else
+                a.xt_lo = base + L.XtLo0.hi;
+        }
+        a.blk_reduce = br;
+        a.blk_split = bs;
+        return a;
+    };
+    int blk_r = 0, blk_s = 0;
+    for (Request *r : ingest) {
+        aux.push_back(aux_of(r, blk_r, blk_s));
+        calls.push_back(call_of(r));
+        blk_r += grouped_reduce_blocks(r->plan->m, r->plan->n, aux.back().wide);
+        blk_s += grouped_split_blocks(r->plan->m, r->plan->n);
+        r->pc += 3;
+    }
+    // Product stage of every grouped request (including the ones just ingested).
+    std::vector<TcProblem> probs[2];
+    std::vector<int> starts[2];
+    int tiles[2] = {0, 0};
+    for (Request *r : s->active) {
+        if (r->state != 1 || !r->grouped)
+            continue;
+        Plan &P = *r->plan;
+        const Op &op = P.ops[r->pc];
+        if (op.kind != OP_TC)
+            continue;
+        const int g = (op.bn == 256) ? 1 : 0;
+        const TcLaunch &l = P.tc[op.idx];
+        for (int q = 0; q < l.nprob; ++q) {
+            TcProblem tp = l.p[q];
+            for (const PatchRec &pr : P.patches)
+                if (pr.kind == OP_TC && pr.launch == op.idx && pr.prob == q) {
+                    if (pr.flags & PT_C_IS_A) {
+                        tp.ep.c0 = r->m.A;
+                        tp.ep.ldc = r->m.lda;
+                    }
+                    if (pr.flags & PT_O_IS_Y) {
+                        tp.ep.o0 = r->m.Y;
+                        tp.ep.ldo = r->m.ldy;
+                        attach_store_maps(tp);
+                    }
+                    if (pr.flags & PT_ALPHA_NEG_TAU)
+                        tp.ep.alpha = -(double)r->m.tau;
+                }
+            tp.patch = 0;
+            starts[g].push_back(tiles[g]);
+            tiles[g] += tc_num_tiles(tp, op.bn);
+            probs[g].push_back(tp);
+        }
+        r->pc += 1;
+        if (P.ops[r->pc].kind == OP_FINAL)
+            fin.push_back(r);
+    }
+    // Finalize records.
+    std::vector<AuxRec> faux;
+    std::vector<CallRec> fcalls;
+    for (Request *r : fin) {
+        faux.push_back(aux_of(r, 0, 0));
+        fcalls.push_back(call_of(r));
+    }
+    // Stage the tables.
+    size_t o_aux = take(sizeof(AuxRec) * aux.size()), o_calls = take(sizeof(CallRec) * calls.size());
+    size_t o_faux = take(sizeof(AuxRec) * faux.size()), o_fcalls = take(sizeof(CallRec) * fcalls.size());
+    size_t o_p[2], o_s[2];
+    for (int g = 0; g < 2; ++g) {
+        starts[g].push_back(tiles[g]);
+        o_p[g] = take(sizeof(TcProblem) * probs[g].size());
+        o_s[g] = take(sizeof(int) * starts[g].size());
+    }
+    if (used > kRingSlotBytes)
+        return SVT_ERR_OOM;
+    std::memcpy(h + o_aux, aux.data(), sizeof(AuxRec) * aux.size());
+    std::memcpy(h + o_calls, calls.data(), sizeof(CallRec) * calls.size());
+    std::memcpy(h + o_faux, faux.data(), sizeof(AuxRec) * faux.size());
+    std::memcpy(h + o_fcalls, fcalls.data(), sizeof(CallRec) * fcalls.size());
+    for (int g = 0; g < 2; ++g) {
+        std::memcpy(h + o_p[g], probs[g].data(), sizeof(TcProblem) * probs[g].size());
+        std::memcpy(h + o_s[g], starts[g].data(), sizeof(int) * starts[g].size());
+    }
+    cudaStream_t st = s->win;
+    if (used && cudaMemcpyAsync(d, h, used, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    auto A = [&](size_t o) { return reinterpret_cast<AuxRec *>(d + o); };
+    auto C = [&](size_t o) { return reinterpret_cast<CallRec *>(d + o); };
+    int launched = 0;
+    if (!ingest.empty()) {
+        const int n = (int)ingest.size();
+        if (grouped_zero_launch(A(o_aux), n, st) != cudaSuccess ||
+            grouped_reduce_launch(A(o_aux), C(o_calls), n, blk_r, st) != cudaSuccess ||
+            grouped_split_launch(A(o_aux), C(o_calls), n, blk_s, st) != cudaSuccess)
+            return SVT_ERR_CUDA;
+        launched += 3;
+    }
+    for (int g = 0; g < 2; ++g) {
+        if (probs[g].empty())
+            continue;
+        TcLaunch L;
+        std::memset(&L, 0, sizeof(L));
+        L.gtab = reinterpret_cast<const TcProblem *>(d + o_p[g]);
+        L.gstart = reinterpret_cast<const int *>(d + o_s[g]);
+        L.gcount = (int)probs[g].size();
+        if (tc_gemm_launch_grouped(L, g ? 256 : 128, tiles[g], ctx->num_sms, st) != cudaSuccess)
+            return SVT_ERR_CUDA;
+        ++launched;
+    }
+    // Requests outside the grouped kinds advance one op with ordinary launches.
+    for (Request *r : single) {
+        CallArgs a{r->m.A, r->m.lda, r->m.tau, r->m.Y, r->m.ldy, r->m.d_status};
+        size_t last = r->pc + 1;
+        if (r->plan->ops[r->pc].kind == OP_MEMSET)
+            last = r->pc + 3;  // memset, reduce, split together
+        svt_status e;
+        {
+            std::lock_guard<std::mutex> g(ctx->mu);
+            e = run_ops(ctx, *r->plan, a, st, r->pc, last);
+        }
+        if (e != SVT_OK)
+            return e;
+        r->pc = last;
+        if (r->pc >= r->plan->ops.size()) {
+            if (plan_status_copy(ctx, *r->plan, &s->h_status[r->slot], st) != SVT_OK ||
+                cudaEventRecord(s->events[r->slot], st) != cudaSuccess)
+                return SVT_ERR_CUDA;
+            r->state = 3;
+        }
+    }
+    if (!fin.empty()) {
+        if (grouped_finalize_launch(A(o_faux), C(o_fcalls), (int)fin.size(), st) != cudaSuccess)
+            return SVT_ERR_CUDA;
+        ++launched;
+        for (Request *r : fin) {
+            r->pc += 1;
+            if (plan_status_copy(ctx, *r->plan, &s->h_status[r->slot], st) != SVT_OK ||
+                cudaEventRecord(s->events[r->slot], st) != cudaSuccess)
+                return SVT_ERR_CUDA;
+            r->state = 3;
+        }
+    }
+    if (cudaEventRecord(s->ring_ev[k], st) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    s->ring_busy[k] = true;
+    s->ring_next = (k + 1) % kRing;
+    ctx->launches += (uint64_t)launched;
+    ++s->windows;
+    return SVT_OK;
+}
+
 // One scheduler tick under s->mu. Returns true if anything happened.
 bool tick(svt_ctx *ctx, ServeState *s)
 {
     bool progress = false;
-    // Retire.
+    // Retire requests whose last op has completed on the device.
     for (auto it = s->active.begin(); it != s->active.end();) {
         Request *r = *it;
+        if (r->state != 3) {
+            ++it;
+            continue;
+        }
         cudaError_t q = cudaEventQuery(s->events[r->slot]);
         if (q == cudaErrorNotReady) {
             ++it;
             continue;
         }
-        r->t_done = now_ms();
-        r->result = (q == cudaSuccess) ? (svt_status)s->h_status[r->slot] : SVT_ERR_CUDA;
-        r->state = 2;
-        s->arena.release(r->ws_off, r->ws_len);
-        s->slot_used[r->slot] = false;
+        finish(s, r, q == cudaSuccess ? (svt_status)s->h_status[r->slot] : SVT_ERR_CUDA);
         it = s->active.erase(it);
         progress = true;
     }
-    // Admit in arrival order.
+    // Admit in arrival order while a slot and workspace are free.
     while (!s->queue.empty() && (int)s->active.size() < kSlots) {
         Request *r = s->queue.front();
         size_t off;
@@ -242,32 +507,46 @@ bool tick(svt_ctx *ctx, ServeState *s)
         s->slot_used[slot] = true;
         r->slot = slot;
         r->ws_off = off;
-        cudaStream_t st = s->streams[s->rr++ % kStreams];
         Plan *plan = nullptr;
         svt_status e;
         {
             std::lock_guard<std::mutex> g(ctx->mu);
             if (ctx->plans.size() > 512)
                 ctx->plans.clear();
-            e = get_plan(ctx, r->m.m, r->m.n, r->opt, off, ctx->ws_bytes - off, &plan);
-            if (e == SVT_OK) {
-                CallArgs a{r->m.A, r->m.lda, r->m.tau, r->m.Y, r->m.ldy, r->m.d_status};
-                e = run_plan(ctx, *plan, a, st);
-            }
-            if (e == SVT_OK)
-                e = plan_status_copy(ctx, *plan, &s->h_status[slot], st);
+            e = get_plan(ctx, r->m.m, r->m.n, r->opt, off, ctx->ws_bytes - kRingBytes - off, &plan);
         }
-        if (e == SVT_OK && cudaEventRecord(s->events[slot], st) != cudaSuccess)
-            e = SVT_ERR_CUDA;
         if (e != SVT_OK) {
-            r->result = e;
-            r->state = 2;
-            r->t_done = now_ms();
-            s->arena.release(off, r->ws_len);
-            s->slot_used[slot] = false;
-        } else {
-            r->state = 1;
-            s->active.push_back(r);
+            finish(s, r, e);
+            progress = true;
+            continue;
+        }
+        r->plan = plan;
+        r->pc = 0;
+        r->grouped = grouped_kinds(*plan);
+        r->state = 1;
+        s->active.push_back(r);
+        progress = true;
+    }
+    // Issue one window if any request has ops left to issue.
+    bool any = false;
+    for (Request *r : s->active)
+        if (r->state == 1)
+            any = true;
+    if (any) {
+        svt_status e = issue_window(ctx, s);
+        if (e == SVT_ERR_NOT_READY)
+            return progress;
+        if (e != SVT_OK) {
+            for (auto it = s->active.begin(); it != s->active.end();) {
+                Request *r = *it;
+                if (r->state == 1) {
+                    cudaStreamSynchronize(s->win);
+                    finish(s, r, e);
+                    it = s->active.erase(it);
+                } else {
+                    ++it;
+                }
+            }
         }
         progress = true;
     }
@@ -280,8 +559,12 @@ void scheduler(svt_ctx *ctx, ServeState *s)
     std::unique_lock<std::mutex> lk(s->mu);
     while (!s->stop) {
         bool progress = tick(ctx, s);
-        if (progress)
+        if (progress) {
+            lk.unlock();  // let submit / poll in between windows
+            std::this_thread::yield();
+            lk.lock();
             continue;
+        }
         if (s->active.empty())
             s->cv.wait_for(lk, std::chrono::milliseconds(5));
         else {
@@ -482,6 +765,15 @@ void serve_shutdown(svt_ctx *ctx)
     s->batches.clear();
     if (s->capture)
         cudaStreamDestroy(s->capture);
+    if (s->win) {
+        cudaStreamSynchronize(s->win);
+        cudaStreamDestroy(s->win);
+    }
+    for (int i = 0; i < kRing; ++i)
+        if (s->ring_ev[i])
+            cudaEventDestroy(s->ring_ev[i]);
+    if (s->h_ring)
+        cudaFreeHost(s->h_ring);
     for (auto &kv : s->tickets)
         delete kv.second;
     for (Request *r : s->queue)
@@ -679,7 +971,7 @@ svt_status svt_serve_submit(svt_ctx_t ctx, const svt_matrix *req, uint64_t *tick
     if (r.prec == SVT_FP64 && (req->m > kF64MaxDim || req->n > kF64MaxDim))
         return SVT_ERR_UNSUPPORTED;
     size_t need = align_up(make_layout(req->m, req->n, r).total, kAlign);
-    if (need > ctx->ws_bytes)
+    if (ctx->ws_bytes < kRingBytes || need > ctx->ws_bytes - kRingBytes)
         return SVT_ERR_OOM;
     ServeState *s;
     {
@@ -690,7 +982,7 @@ svt_status svt_serve_submit(svt_ctx_t ctx, const svt_matrix *req, uint64_t *tick
     if (!s->started) {
         if (start_workers(ctx, s) != SVT_OK)
             return SVT_ERR_CUDA;
-        s->arena.reset(ctx->ws_bytes);
+        s->arena.reset(ctx->ws_bytes - kRingBytes);
         s->thread = std::thread(scheduler, ctx, s);
         s->started = true;
     }

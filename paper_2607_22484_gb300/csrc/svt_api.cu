@@ -664,7 +664,8 @@ __global__ void prep_kernel(const float *__restrict__ A, int64_t lda, int wide, 
 
 } // namespace
 
-svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s)
+svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, size_t first,
+                   size_t last)
 {
     uint8_t *base = ctx->ws + P.ws_base;
     const Layout &L = P.lay;
@@ -676,7 +677,11 @@ svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s)
     const bool skipP = P.opt.mode == SVT_MODE_RANK_R;
     cudaError_t err = cudaSuccess;
     int cur_final = P.opt.iters % 2;
-    for (const Op &op : P.ops) {
+    int launched = 0;
+    for (size_t oi = first; oi < last && oi < P.ops.size(); ++oi) {
+        const Op &op = P.ops[oi];
+        if (op.kind != OP_MEMSET)
+            ++launched;
         switch (op.kind) {
         case OP_MEMSET:
             // scalars, status and Gram diagonal are contiguous from L.scal
@@ -782,8 +787,13 @@ svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s)
         if (err != cudaSuccess)
             return SVT_ERR_CUDA;
     }
-    ctx->launches += (uint64_t)P.kernel_launches;
+    ctx->launches += (uint64_t)launched;
     return SVT_OK;
+}
+
+svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s)
+{
+    return run_ops(ctx, P, a, s, 0, P.ops.size());
 }
 
 svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_t ws_base,
