@@ -207,6 +207,131 @@ def torch_plain_fp32(A, tau, coefs, theta_from="gram"):
     return 0.5 * (A - tau * P) @ (torch.eye(n, device=A.device) + S)
 
 
+def batch_extra(ctx_cls, pkg, torch, dev, steps=5, warmup=2):
+    """Grouped batch: 256 low-rank + noise matrices, sizes log-uniform 128-1024,
+    aspect 1, 2, 1/2, BF16 tier, 20 steps, one svt_batch call per step."""
+    import svt_workloads as wl
+    items = wl.batch_recipe(256)
+    As = [torch.from_numpy(it.matrix()).to(dev) for it in items]
+    taus = [it.tau for it in items]
+    outs = [torch.empty_like(a) for a in As]
+    opts = {"iters": ITERS, "prec": "bf16"}
+    ctx = ctx_cls(dev.index or 0, workspace_bytes=1 << 20)
+    for _ in range(warmup):
+        ctx.batch(As, taus, outs=outs, opts=opts)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record()
+    for _ in range(steps):
+        ctx.batch(As, taus, outs=outs, opts=opts)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # the same matrices one at a time through svt_polar
+    single = ctx_cls(dev.index or 0, workspace_bytes=1 << 20)
+    for a, t, y in zip(As, taus, outs):
+        single.polar(a, t, out=y, **opts)
+    torch.cuda.synchronize()
+    e0.record()
+    for a, t, y in zip(As, taus, outs):
+        single.polar(a, t, out=y, **opts)
+    e1.record()
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    fl = sum(alg_flops(it.m, it.n, ITERS) for it in items)
+    return {"workload": "256 low-rank+noise matrices, size log-uniform 128-1024, aspect {1,2,1/2}, "
+                        "rank 5-50, tau = noise edge + 0.5, BF16 tier, 20 steps",
+            "solves_per_s": len(items) / (ms / 1e3), "ms_per_batch": ms,
+            "alg_tflops": fl / (ms / 1e3) / 1e12,
+            "one_at_a_time_solves_per_s": len(items) / (ms1 / 1e3),
+            "speedup_vs_one_at_a_time": ms1 / ms,
+            "launches": "grouped: one product launch per stage for all matrices, CUDA graph"}
+
+
+def serving_extra(ctx_cls, pkg, torch, dev, n_req=200):
+    """Poisson stream through svt_serve_submit / svt_serve_poll: sizes log-uniform
+    256-8192 (rounded to powers of two), aspect 1, 2, 1/2, 30 % FP32 tier. Capacity
+    is the closed-loop throughput of the same stream; open-loop runs at 0.5, 0.8
+    and 0.95 of it report p50 / p99 submit-to-completion latency."""
+    import math as _m
+    import svt_workloads as wl
+    reqs = wl.poisson_requests(n_req, rate_per_s=1.0)
+    shapes = {}
+    def cls(v):
+        return 1 << max(7, int(round(_m.log2(v))))
+    pool = {}
+    plan = []
+    for r in reqs:
+        m, n = cls(r.m), cls(r.n)
+        key = (m, n)
+        if key not in pool:
+            a = wl.low_rank_plus_noise(m, n, 20, 5000 + len(pool), 2.0, 10.0)
+            pool[key] = (torch.from_numpy(a).to(dev), wl.noise_edge(m, n) + 0.5, [])
+        plan.append((key, r.tier))
+    ctx = ctx_cls(dev.index or 0, workspace_bytes=16 << 30)
+
+    def out_for(key, busy):
+        a, tau, ys = pool[key]
+        for y in ys:
+            if y.data_ptr() not in busy:
+                return y
+        y = torch.empty_like(a)
+        ys.append(y)
+        return y
+
+    def run(arrivals):
+        import time as _t
+        t0 = _t.perf_counter()
+        pending, lat, busy, failed = {}, [], set(), 0
+        i = 0
+        while i < len(plan) or pending:
+            now = _t.perf_counter() - t0
+            while i < len(plan) and (arrivals is None or arrivals[i] <= now):
+                key, tier = plan[i]
+                a, tau, _ = pool[key]
+                y = out_for(key, busy)
+                busy.add(y.data_ptr())
+                tk = ctx.submit(a, tau, y, iters=ITERS, prec=tier)
+                pending[tk] = y.data_ptr()
+                i += 1
+            for tk in list(pending):
+                st, l = ctx.poll(tk)
+                if st != pkg.binding.ERR_NOT_READY:
+                    if st == 0:
+                        lat.append(l)
+                    else:
+                        failed += 1
+                    busy.discard(pending.pop(tk))
+                    ctx.release(tk)
+            _t.sleep(0.0002)
+        wall = _t.perf_counter() - t0
+        lat.sort()
+        if failed:
+            raise RuntimeError(f"{failed} serving requests failed")
+        return wall, lat
+
+    run(None)  # warm-up: plans and first launches
+    wall, lat = run(None)
+    cap = len(plan) / wall
+    out = {"workload": f"{n_req} requests, sizes log-uniform 256-8192 rounded to powers of two, "
+                       "aspect {1,2,1/2}, rank-20 signal + noise, 70% BF16 / 30% FP32 tier, 20 steps",
+           "capacity_req_per_s": cap, "loads": []}
+    import random as _r
+    for load in (0.5, 0.8, 0.95):
+        rate = load * cap
+        rng = _r.Random(1005)
+        t, arr = 0.0, []
+        for _ in plan:
+            t += rng.expovariate(rate)
+            arr.append(t)
+        wall, lat = run(arr)
+        out["loads"].append({"offered": load, "rate_req_per_s": rate,
+                             "throughput_req_per_s": len(plan) / wall,
+                             "p50_ms": lat[len(lat) // 2],
+                             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]})
+    return out
+
+
 def run_ours(args, n):
     import numpy as np
     import torch
@@ -369,6 +494,9 @@ def run_ours(args, n):
         "status": pkg.status_str(st), "output_finite": finite,
         "clocks": clocks,
     }
+    if world == 1 and not args.no_extras:
+        line["batch"] = batch_extra(pkg.Context, pkg, torch, dev)
+        line["serving"] = serving_extra(pkg.Context, pkg, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
         est, desc, cores = oracle_sample(n, 1002, 96, repeats=1)
         line["cpu_baseline"] = {"value": 1.0 / est[0], "unit": "solves/s", "cores": cores,
@@ -387,6 +515,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batch and serving measurements")
     ap.add_argument("--only-timed", action="store_true",
                     help="run only the warm-up and timed solves (for profiler launch lists)")
     args = ap.parse_args()

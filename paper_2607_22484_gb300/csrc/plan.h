@@ -129,7 +129,7 @@ struct svt_ctx {
     uint8_t *ws = nullptr;
     size_t ws_bytes = 0;
     uint64_t launches = 0;
-    std::map<svt::Key, std::unique_ptr<svt::Plan>> plans;
+    std::map<svt::Key, std::shared_ptr<svt::Plan>> plans;  // users may hold their own reference
     std::mutex mu;
     ServeState *serve = nullptr;
     // Optional per-launch timing of the tensor-core kernel (svt_ctx_profile).
@@ -141,8 +141,13 @@ struct svt_ctx {
 };
 
 namespace svt {
+// Look up or build the plan of a solve (under ctx->mu). `keep` (nullable) receives
+// a reference that keeps the plan alive across cache evictions.
 svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_t ws_base,
-                    size_t ws_avail, Plan **out, int force_bn = 0);
+                    size_t ws_avail, Plan **out, int force_bn = 0,
+                    std::shared_ptr<Plan> *keep = nullptr);
+// Drop cached plans nobody else holds once the cache exceeds max_entries (under ctx->mu).
+void evict_plans(svt_ctx *ctx, size_t max_entries);
 svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s);
 // Ops [first, last) of a plan only (the serving loop advances requests op by op).
 svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, size_t first,

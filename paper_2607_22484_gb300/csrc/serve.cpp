@@ -108,6 +108,7 @@ struct Request {
     int state = 0;  // 0 queued, 1 running (ops being issued), 3 all issued, 2 done
     svt_status result = SVT_OK;
     Plan *plan = nullptr;
+    std::shared_ptr<Plan> plan_ref;  // keeps the plan alive while ops are in flight
     size_t pc = 0;          // next op of the plan to issue
     bool grouped = false;   // ops limited to the kinds the grouped kernels cover
 };
@@ -247,6 +248,8 @@ bool grouped_kinds(const Plan &P)
 
 void finish(ServeState *s, Request *r, svt_status st)
 {
+    r->plan = nullptr;
+    r->plan_ref.reset();
     r->result = st;
     r->state = 2;
     r->t_done = now_ms();
@@ -511,9 +514,9 @@ bool tick(svt_ctx *ctx, ServeState *s)
         svt_status e;
         {
             std::lock_guard<std::mutex> g(ctx->mu);
-            if (ctx->plans.size() > 512)
-                ctx->plans.clear();
-            e = get_plan(ctx, r->m.m, r->m.n, r->opt, off, ctx->ws_bytes - kRingBytes - off, &plan);
+            evict_plans(ctx, 512);  // plans of active requests stay alive through plan_ref
+            e = get_plan(ctx, r->m.m, r->m.n, r->opt, off, ctx->ws_bytes - kRingBytes - off, &plan,
+                         0, &r->plan_ref);
         }
         if (e != SVT_OK) {
             finish(s, r, e);

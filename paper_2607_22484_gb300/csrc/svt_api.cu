@@ -796,17 +796,31 @@ svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s)
     return run_ops(ctx, P, a, s, 0, P.ops.size());
 }
 
+void evict_plans(svt_ctx *ctx, size_t max_entries)
+{
+    if (ctx->plans.size() <= max_entries)
+        return;
+    for (auto it = ctx->plans.begin(); it != ctx->plans.end();) {
+        if (it->second.use_count() == 1)
+            it = ctx->plans.erase(it);
+        else
+            ++it;
+    }
+}
+
 svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_t ws_base,
-                    size_t ws_avail, Plan **out, int force_bn)
+                    size_t ws_avail, Plan **out, int force_bn, std::shared_ptr<Plan> *keep)
 {
     Key k{m, n, r.iters, r.prec, r.schedule, r.norm, r.polish, r.mode, r.hp_steps, r.ell0, r.delta,
           ws_base, force_bn};
     auto it = ctx->plans.find(k);
     if (it != ctx->plans.end()) {
         *out = it->second.get();
+        if (keep)
+            *keep = it->second;
         return SVT_OK;
     }
-    auto plan = std::make_unique<Plan>();
+    auto plan = std::make_shared<Plan>();
     plan->m = m;
     plan->n = n;
     plan->wide = n > m;
@@ -825,6 +839,8 @@ svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_
     if (!b.build())
         return SVT_ERR_CUDA;
     *out = plan.get();
+    if (keep)
+        *keep = plan;
     ctx->plans[k] = std::move(plan);
     return SVT_OK;
 }

@@ -149,3 +149,33 @@ def test_batch_graph_replay_new_data_and_mixed_fallback():
                                                  return_svd=True)
         if oracle.gap(s, it.tau) >= 0.05:
             assert oracle.relerr(y.cpu().numpy(), exact) < (2e-2 if o["prec"] == "bf16" else 1e-4)
+
+
+def test_serving_plan_cache_churn():
+    """Many distinct request shapes: the context's plan cache evicts entries while
+    other requests are in flight; every result must still be right."""
+    rng = np.random.default_rng(123)
+    ctx = pkg.Context(0, workspace_bytes=64 << 20)
+    reqs = []
+    for i in range(600):
+        m, n = int(rng.integers(24, 97)), int(rng.integers(24, 97))
+        a = wl.low_rank_plus_noise(m, n, 4, 9000 + i, 2.0, 10.0)
+        tau = wl.noise_edge(m, n) + 0.5
+        A = torch.from_numpy(a).cuda()
+        Y = torch.full_like(A, float("nan"))
+        reqs.append((a, tau, A, Y, ctx.submit(A, tau, Y, iters=12, prec="bf16")))
+    done = {}
+    t0 = time.time()
+    while len(done) < len(reqs) and time.time() - t0 < 120:
+        for a, tau, A, Y, t in reqs:
+            if t not in done:
+                st, _ = ctx.poll(t)
+                if st != pkg.binding.ERR_NOT_READY:
+                    done[t] = st
+        time.sleep(0.001)
+    assert len(done) == len(reqs)
+    assert all(st == 0 for st in done.values())
+    for a, tau, A, Y, t in reqs[::37]:
+        exact, (u, s, v) = oracle.svt_definition(a.astype(np.float64), tau, return_svd=True)
+        if oracle.gap(s, tau) >= 0.05:
+            assert oracle.relerr(Y.cpu().numpy(), exact) < 2e-2
