@@ -262,6 +262,20 @@ svt_status svt_ctx_profile_read(svt_ctx_t ctx, double *tc_ms, double *tc_flops,
                                 uint64_t *tc_launches);
 
 /*
+ * Autotuner for the product kernel's tile width. Runs the svt_polar_ex solve of
+ * this A (m x n, lda), tau and options (NULL = defaults) once as warm-up and `reps`
+ * times timed, with 128 x 128 and with 128 x 256 tiles, times every product
+ * launch with CUDA events on `stream`, and stores the faster width per launch in
+ * the context. Later svt_polar / svt_polar_ex calls with the same shape and
+ * options use the tuned widths. Y receives A_tau. Synchronises `stream`.
+ * Errors: as svt_polar_ex; SVT_ERR_BUSY while serving requests are in flight.
+ * The FP64 tier has no tile choice (returns SVT_OK without work).
+ */
+svt_status svt_autotune(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int64_t lda,
+                        float tau, const svt_options *opt, float *Y, int64_t ldy, int reps,
+                        void *stream);
+
+/*
  * svt_polar_noalloc: the svt_polar_ex solve without any workspace from the
  * caller and without allocating device memory. (The paper has no counterpart:
  * this entry point exists for callers, not for the method.)

@@ -38,7 +38,7 @@ EXPORTS = [
     "svt_ctx_create", "svt_ctx_destroy", "svt_polar", "svt_polar_ex", "svt_batch",
     "svt_batch_workspace_bytes", "svt_serve_submit", "svt_serve_poll", "svt_serve_release",
     "svt_ctx_sync", "svt_schedule_coeffs", "svt_debug_gemm_bf16", "svt_ctx_launch_count",
-    "svt_ctx_profile", "svt_ctx_profile_read", "svt_polar_noalloc",
+    "svt_ctx_profile", "svt_ctx_profile_read", "svt_polar_noalloc", "svt_autotune",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -101,6 +101,8 @@ def lib():
         L.svt_ctx_launch_count.argtypes = [vp]
         L.svt_ctx_launch_count.restype = ctypes.c_uint64
         L.svt_ctx_profile.argtypes = [vp, i32]
+        L.svt_autotune.argtypes = [vp, vp, i64, i64, i64, ctypes.c_float, ctypes.POINTER(Options),
+                                   vp, i64, i32, vp]
         L.svt_polar_noalloc.argtypes = [i32, vp, i64, i64, i64, ctypes.c_float,
                                         ctypes.POINTER(Options), vp, i64, vp, vp]
         L.svt_ctx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
@@ -245,6 +247,22 @@ class Context:
                                   ctypes.c_float(tau), ctypes.byref(o), ctypes.c_void_p(y_ptr),
                                   ldy, ctypes.c_void_p(st_ptr), ctypes.c_void_p(_stream_ptr(stream))),
                "svt_polar_ex")
+        return out
+
+    def autotune(self, A, tau: float, out=None, reps: int = 2, stream=None, **opts):
+        """Pick the product kernel's tile width per launch for this shape and options
+        (svt_autotune); later polar() calls with them use the tuned plan."""
+        import torch
+        a_ptr, m, n, lda = _f32_matrix(A, "A")
+        if out is None:
+            out = torch.empty((m, n), dtype=torch.float32, device=A.device)
+        y_ptr, _, _, ldy = _f32_matrix(out, "out")
+        o = make_options(**opts)
+        self.ensure_workspace(workspace_bytes(m, n, **opts))
+        _check(lib().svt_autotune(self.handle, ctypes.c_void_p(a_ptr), m, n, lda,
+                                  ctypes.c_float(tau), ctypes.byref(o), ctypes.c_void_p(y_ptr),
+                                  ldy, int(reps), ctypes.c_void_p(_stream_ptr(stream))),
+               "svt_autotune")
         return out
 
     def polar_host(self, A_host, tau: float, out_host=None, stream=None, **opts):

@@ -87,8 +87,28 @@ struct Plan {
     std::vector<double> tc_flops;   // algorithmic flops of each tensor-core launch
     int tc_launches_per_solve = 0;
     int kernel_launches = 0;
-    int force_bn = 0;               // 0: tile width per launch; 128 / 256: fixed (grouped batches)
+    int force_bn = 0;               // 0: tile width per launch; 128 / 256: fixed (grouped batches);
+                                    // -1: per-launch widths from bn_choice (autotuned)
+    std::vector<int> bn_choice;     // tile width of each product launch (autotuned plans)
 };
+
+// Autotuned tile widths of one (shape, options): one entry per product launch.
+struct TuneKey {
+    int64_t m, n;
+    int iters, prec, schedule, norm, polish, mode, hp_steps;
+    double ell0, delta;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(m, n, iters, prec, schedule, norm, polish, mode, hp_steps, ell0, delta) <
+               std::tie(o.m, o.n, o.iters, o.prec, o.schedule, o.norm, o.polish, o.mode,
+                        o.hp_steps, o.ell0, o.delta);
+    }
+};
+inline TuneKey tune_key(int64_t m, int64_t n, const Resolved &r)
+{
+    return TuneKey{m, n, r.iters, r.prec, r.schedule, r.norm, r.polish, r.mode, r.hp_steps,
+                   r.ell0, r.delta};
+}
 
 struct Key {
     int64_t m, n;
@@ -138,6 +158,7 @@ struct svt_ctx {
     struct ProfRec { cudaEvent_t a, b; double flops; };
     std::vector<ProfRec> prof_pending;
     size_t prof_next = 0;
+    std::map<svt::TuneKey, std::vector<int>> tuning;  // svt_autotune results
 };
 
 namespace svt {

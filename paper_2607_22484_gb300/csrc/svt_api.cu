@@ -354,8 +354,10 @@ struct Builder {
         for (const Prod &q : prods)
             if (q.N > 128)
                 bn = 256;
-        if (plan->force_bn)
+        if (plan->force_bn > 0)
             bn = plan->force_bn;
+        else if (plan->force_bn < 0 && plan->tc.size() < plan->bn_choice.size())
+            bn = plan->bn_choice[plan->tc.size()];
         TcLaunch l;
         std::memset(&l, 0, sizeof(l));
         l.nprob = (int)prods.size();
@@ -828,6 +830,12 @@ svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_
     plan->lay = make_layout(m, n, r);
     plan->ws_base = ws_base;
     plan->force_bn = force_bn;
+    if (force_bn < 0) {
+        auto t = ctx->tuning.find(tune_key(m, n, r));
+        if (t == ctx->tuning.end())
+            return SVT_ERR_INVALID;
+        plan->bn_choice = t->second;
+    }
     if (plan->lay.total > ws_avail)
         return SVT_ERR_OOM;
     plan->coef.assign((size_t)std::max(1, 3 * r.iters), 0.0);
@@ -991,11 +999,77 @@ svt_status svt_polar_ex(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int
     if (cudaSetDevice(ctx->device) != cudaSuccess)
         return SVT_ERR_CUDA;
     Plan *plan = nullptr;
-    st = get_plan(ctx, m, n, r, 0, ctx->ws_bytes, &plan);
+    const int fbn = ctx->tuning.count(tune_key(m, n, r)) ? -1 : 0;
+    st = get_plan(ctx, m, n, r, 0, ctx->ws_bytes, &plan, fbn);
     if (st != SVT_OK)
         return st;
     CallArgs a{A, lda, tau, Y, ldy, d_status};
     return run_plan(ctx, *plan, a, static_cast<cudaStream_t>(stream));
+}
+
+svt_status svt_autotune(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int64_t lda,
+                        float tau, const svt_options *opt, float *Y, int64_t ldy, int reps,
+                        void *stream)
+{
+    if (!ctx)
+        return SVT_ERR_INVALID;
+    svt_status st = validate(A, m, n, lda, tau, Y, ldy);
+    if (st != SVT_OK)
+        return st;
+    Resolved r;
+    if (!resolve(opt, &r) || reps < 1)
+        return SVT_ERR_INVALID;
+    if (r.prec == SVT_FP64)
+        return SVT_OK;  // the FP64 tier has no tile choice
+    if (serve_busy(ctx))
+        return SVT_ERR_BUSY;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CallArgs a{A, lda, tau, Y, ldy, nullptr};
+    const int widths[2] = {128, 256};
+    std::vector<double> ms[2];
+    const bool prev_profile = ctx->profile;
+    for (int w = 0; w < 2; ++w) {
+        Plan *plan = nullptr;
+        st = get_plan(ctx, m, n, r, 0, ctx->ws_bytes, &plan, widths[w]);
+        if (st != SVT_OK)
+            return st;
+        st = run_plan(ctx, *plan, a, s);  // warm-up
+        if (st != SVT_OK)
+            return st;
+        ctx->profile = true;
+        ctx->prof_pending.clear();
+        ctx->prof_next = 0;
+        for (int k = 0; k < reps; ++k) {
+            st = run_plan(ctx, *plan, a, s);
+            if (st != SVT_OK) {
+                ctx->profile = prev_profile;
+                return st;
+            }
+        }
+        const size_t per = plan->tc.size();
+        ms[w].assign(per, 0.0);
+        for (size_t i = 0; i < ctx->prof_pending.size(); ++i) {
+            auto &pr = ctx->prof_pending[i];
+            if (cudaEventSynchronize(pr.b) != cudaSuccess) {
+                ctx->profile = prev_profile;
+                return SVT_ERR_CUDA;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, pr.a, pr.b);
+            ms[w][i % per] += t;
+        }
+        ctx->prof_pending.clear();
+        ctx->prof_next = 0;
+        ctx->profile = prev_profile;
+    }
+    std::vector<int> choice(ms[0].size());
+    for (size_t i = 0; i < choice.size(); ++i)
+        choice[i] = (ms[0][i] < ms[1][i]) ? 128 : 256;
+    ctx->tuning[tune_key(m, n, r)] = choice;
+    return SVT_OK;
 }
 
 svt_status svt_polar(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int64_t lda, float tau,

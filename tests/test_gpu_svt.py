@@ -158,3 +158,14 @@ def test_full_size_4096_known_spectrum(ctx):
     err = oracle.relerr(y, exact)
     print(f"4096^2 BF16 relerr {err:.3e}")
     assert err < 2e-2
+
+
+def test_autotuned_plan_matches_oracle(ctx):
+    """svt_autotune picks a tile width per launch; the tuned solve stays correct."""
+    a = _gap_matrix(640, 512, seed=21)
+    exact = oracle.svt_definition(a.astype(np.float64), 0.3)
+    dev = torch.from_numpy(a).cuda()
+    ctx.autotune(dev, 0.3, iters=20, prec="bf16")
+    y = ctx.polar(dev, 0.3, iters=20, prec="bf16")
+    torch.cuda.synchronize()
+    assert oracle.relerr(y.cpu().numpy(), exact) < 2e-2
