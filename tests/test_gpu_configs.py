@@ -1,0 +1,102 @@
+"""Full-size rectangular cases (both branches, Corollary 1) and the
+error-vs-tau / error-vs-iterations curves of the gap-free Marchenko-Pastur case."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import schedule as osch
+from oracle import spectral
+import svt_workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+pkg = pytest.importorskip("paper_2607_22484_gb300")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return pkg.Context(0, workspace_bytes=64 << 20)
+
+
+def _known(m, n, seed):
+    """m x n with 64 singular values in [1.5, 10] and the rest in [0, 0.5] (tau = 1
+    sits 0.5 = 5 % of sigma_max from both groups); returns A, Q1, sigma, Q2."""
+    rng = np.random.default_rng(seed)
+    k = min(m, n)
+    sig = np.concatenate([rng.uniform(1.5, 10.0, 64), rng.uniform(0.0, 0.5, k - 64)])
+    sig[0] = 10.0
+    q1 = np.linalg.qr(rng.standard_normal((m, k)))[0]
+    q2 = np.linalg.qr(rng.standard_normal((n, k)))[0]
+    a = ((q1 * sig) @ q2.T).astype(np.float32)
+    return a, q1, sig, q2
+
+
+@pytest.mark.parametrize("shape", [(8192, 2048), (2048, 8192)])
+def test_rectangular_full_size_and_corollary(ctx, shape):
+    m, n = shape
+    a, q1, sig, q2 = _known(m, n, seed=m + 3 * n)
+    tau = 1.0
+    ctx.ensure_workspace(pkg.workspace_bytes(m, n, prec="bf16"))
+    dev = torch.from_numpy(a).cuda()
+    y = ctx.polar(dev, tau, iters=20, prec="bf16")
+    torch.cuda.synchronize()
+    keep = sig > tau
+    exact = (q1[:, keep] * (sig[keep] - tau)) @ q2[:, keep].T
+    err = oracle.relerr(y.cpu().numpy(), exact)
+    assert err < 2e-2, err
+    # Corollary 1: tau between sigma_65 (<= 0.5) and sigma_64 (>= 1.5) gives [A]_64
+    y = ctx.polar(dev, tau, iters=20, prec="bf16", mode="rank_r")
+    torch.cuda.synchronize()
+    best = (q1[:, keep] * sig[keep]) @ q2[:, keep].T
+    err = oracle.relerr(y.cpu().numpy(), best)
+    assert err < 2e-2, err
+
+
+def test_error_curves_marchenko_pastur(ctx):
+    """No gap: the tolerances do not bind; record error vs tau and vs iterations
+    against the oracle, and check the expected shape (error falls, then levels)."""
+    n = 1024
+    a = wl.marchenko_pastur(n, seed=1002)
+    u, s, v = oracle.jacobi_svd(a.astype(np.float64))
+    dev = torch.from_numpy(a).cuda()
+    taus = [0.25, 0.5, 1.0, 1.5]
+    ks = [4, 6, 8, 10, 12, 16, 20]
+    rows = []
+    table = {}
+    for tau in taus:
+        exact = (u * np.maximum(s - tau, 0)) @ v.T
+        for k in ks:
+            res = {}
+            for prec in ("bf16", "fp32"):
+                y = ctx.polar(dev, tau, iters=k, prec=prec)
+                torch.cuda.synchronize()
+                res[prec] = oracle.relerr(y.cpu().numpy(), exact)
+            delta = 0.01
+            coefs, _ = osch.pe5_schedule(k, 1e-3, delta)
+            pred = spectral.predict(u, s, v, tau, coefs, coefs, "gram", "gram")
+            res["model"] = oracle.relerr(pred, exact)
+            table[(tau, k)] = res
+            rows.append(f"| {tau} | {k} | {res['bf16']:.3e} | {res['fp32']:.3e} | {res['model']:.3e} |")
+    out = os.environ.get("SVT_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "error_curves_mp1024.md"), "w") as f:
+            f.write("| tau | iters | BF16 tier | FP32 tier | exact-arithmetic model |\n|---|---|---|---|---|\n")
+            f.write("\n".join(rows) + "\n")
+    for tau in taus:
+        bf = [table[(tau, k)]["bf16"] for k in ks]
+        assert all(np.isfinite(bf))
+        # Section 3, Fig. 1: the error falls quickly between 4 and 6 iterations ...
+        assert table[(tau, 6)]["bf16"] < 0.1 * table[(tau, 4)]["bf16"]
+        # ... and then stagnates (BF16 rounding floor)
+        assert table[(tau, 20)]["bf16"] < 2.0 * table[(tau, 6)]["bf16"]
+        # the FP32-class tier sits far below BF16 once the iteration has converged
+        assert table[(tau, 20)]["fp32"] < 1e-3
+        assert table[(tau, 20)]["fp32"] < 0.1 * table[(tau, 20)]["bf16"]
+        # and before convergence both tiers follow the exact-arithmetic model
+        assert abs(table[(tau, 4)]["fp32"] - table[(tau, 4)]["model"]) < 0.05 * table[(tau, 4)]["model"]
+    # worse for tau near sigma_max (about 2 here) than near sigma_min
+    assert table[(1.5, 20)]["bf16"] > table[(0.25, 20)]["bf16"]
