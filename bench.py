@@ -360,7 +360,7 @@ def run_ours(args, n):
     ctx = pkg.Context(local, workspace_bytes=pkg.workspace_bytes(n, n, iters=ITERS, prec="bf16"))
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
-    opts = dict(iters=ITERS, prec="bf16")
+    opts = dict(iters=ITERS, prec="bf16", fuse=not args.no_fuse)
 
     if not args.no_autotune:
         ctx.autotune(A, TAU, out=Y, reps=2, **opts)  # tile width per product launch
@@ -518,6 +518,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fuse", action="store_true",
+                    help="one launch per product stage instead of the fused persistent launch")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default tile widths instead of svt_autotune")
     ap.add_argument("--no-extras", action="store_true",

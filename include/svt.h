@@ -32,7 +32,10 @@
  *     svt_ctx_sync / svt_serve_poll.
  *   - Streams are cudaStream_t passed as void* (NULL = legacy default stream).
  *   - A context is not thread-safe, except svt_serve_submit / svt_serve_poll,
- *     which may be called from any thread.
+ *     which may be called from any thread. All solves of one context share its
+ *     workspace, so their work must be ordered on the device (one stream, or
+ *     streams synchronised by the caller); serving must be idle while
+ *     svt_polar / svt_batch run (they return SVT_ERR_BUSY otherwise).
  */
 #ifndef SVT_H
 #define SVT_H
@@ -99,6 +102,10 @@ typedef struct {
                                    (default 1; ignored for SVT_FP64, which
                                    polishes in FP64) */
     svt_mode mode;              /* default SVT_MODE_SVT */
+    int fuse;                   /* 1 (default): all product launches of a solve run as
+                                   one persistent launch whose tiles wait on the
+                                   problems they read (device-side dependency
+                                   counters); 0: one launch per product stage */
     int hp_steps;               /* SVT_BF16 only: number of leading S-chain steps run
                                    in the FP32-class tier (the shifted Gram's small
                                    eigenvalues sigma^2 - tau^2 do not survive BF16

@@ -46,7 +46,8 @@ NOALLOC_SCRATCH_BYTES = 32 << 20
 class Options(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("prec", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("norm", ctypes.c_int), ("ell0", ctypes.c_double), ("delta", ctypes.c_double),
-                ("polish", ctypes.c_int), ("mode", ctypes.c_int), ("hp_steps", ctypes.c_int)]
+                ("polish", ctypes.c_int), ("mode", ctypes.c_int), ("fuse", ctypes.c_int),
+                ("hp_steps", ctypes.c_int)]
 
 
 class Matrix(ctypes.Structure):
@@ -125,7 +126,8 @@ def _check(st: int, where: str):
 
 
 def make_options(iters: int = 20, prec="bf16", schedule="auto", norm="auto", ell0: float = 1e-3,
-                 delta: float = -1.0, polish: bool = True, mode="svt", hp_steps: int = -1) -> Options:
+                 delta: float = -1.0, polish: bool = True, mode="svt", hp_steps: int = -1,
+                 fuse: bool = True) -> Options:
     o = Options()
     lib().svt_options_default(ctypes.byref(o))
     o.iters = int(iters)
@@ -137,6 +139,7 @@ def make_options(iters: int = 20, prec="bf16", schedule="auto", norm="auto", ell
     o.polish = 1 if polish else 0
     o.mode = MODE[mode] if isinstance(mode, str) else int(mode)
     o.hp_steps = int(hp_steps)
+    o.fuse = 1 if fuse else 0
     return o
 
 

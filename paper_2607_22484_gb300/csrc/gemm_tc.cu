@@ -122,6 +122,38 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ int ld_acquire_gpu(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait until *counter >= target (another CTA's completion count).
+__device__ bool wait_counter(const int *counter, int target, volatile int *abort_flag, int *status,
+                             uint64_t limit_ns)
+{
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (ld_acquire_gpu(counter) >= target)
+            return true;
+        if ((it & 63u) == 63u) {
+            if (*abort_flag)
+                return false;
+            uint64_t now = global_timer_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > limit_ns) {
+                *abort_flag = 1;
+                if (status)
+                    atomicCAS(status, 0, (int)SVT_ERR_TIMEOUT);
+                return false;
+            }
+            __nanosleep(64);
+        }
+    }
+}
 
 // Shared-memory matrix descriptor for a K-major operand tile laid out by TMA
 // with 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
@@ -595,7 +627,9 @@ __device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiOver
 
 // --------------------------------------------------------------- kernel
 
-template <int BN, int STAGES>
+constexpr int kRingTiles = 4;  // fused launches: tile ids in flight between the roles
+
+template <int BN, int STAGES, bool CHAIN>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcLaunch L)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -614,6 +648,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int *skip_flag = reinterpret_cast<int *>(tmem_slot + 2);
+    // Fused launches: a ring of tile ids from the producer to the MMA and epilogue roles.
+    uint64_t *rfull = reinterpret_cast<uint64_t *>(
+        (reinterpret_cast<uintptr_t>(tmem_slot + 3) + 7) & ~static_cast<uintptr_t>(7));
+    uint64_t *rempty = rfull + kRingTiles;
+    volatile int *tring = reinterpret_cast<volatile int *>(rempty + kRingTiles);
+    const CallRec *calls = L.calls ? L.calls : &L.call_inline;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -629,6 +669,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             mbar_init(&tempty[b], 32 * kEpiWarps);
         }
         mbar_init(drain, 1);
+        for (int i = 0; i < kRingTiles; ++i) {
+            mbar_init(&rfull[i], 1);
+            mbar_init(&rempty[i], 1 + kEpiWarps);
+        }
         *abort_flag = 0;
         // A solve whose earlier launch already timed out does no further work.
         *skip_flag = (status0 && *reinterpret_cast<volatile int *>(status0) == (int)SVT_ERR_TIMEOUT);
@@ -652,12 +696,38 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         uint32_t phase = 0;
         uint32_t issued = 0, issued_parity = 0;  // bit s: stage s loaded / parity of its last load
         bool ok = true;
-        for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        int ri = 0;
+        uint32_t rphase = 0;
+        for (int it = 0, t = blockIdx.x; ok; ++it, t += gridDim.x) {
+            if (CHAIN) {
+                // Take the next tile in table order and hand its id to the other roles.
+                if (!mbar_wait(&rempty[ri], rphase ^ 1u, abort_flag, status0, kWaitTimeoutNs))
+                    break;
+                t = atomicAdd(L.tile_counter, 1);
+                tring[ri] = (t < total) ? t : -1;
+                mbar_arrive(&rfull[ri]);
+                if (++ri == kRingTiles) {
+                    ri = 0;
+                    rphase ^= 1u;
+                }
+            }
+            if (t >= total)
+                break;
             TileCoord tc = decode_tile<BN>(L, t);
             if (!tc.valid)
                 continue;
             const TcProblem &P = prob_at(L, tc.prob);
             const int kblocks = (P.K + kBK - 1) / kBK;
+            if (CHAIN) {
+                // Operands are results of earlier problems: wait until they are complete.
+                for (int d = 0; d < 2 && ok; ++d)
+                    if (P.dep[d] >= 0)
+                        ok = wait_counter(&L.done[P.dep[d]], P.dep_target[d], abort_flag, status0,
+                                          kWaitTimeoutNs);
+                fence_async_global();  // the TMA reads below come after the acquire
+                if (!ok)
+                    break;
+            }
             for (int sg = 0; sg < P.nseg && ok; ++sg) {
                 const CUtensorMap *mL = &P.mapL[P.segL[sg]];
                 const CUtensorMap *mR = &P.mapR[P.segR[sg]];
@@ -692,7 +762,23 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         int buf = 0;
         uint32_t tphase = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        int ri = 0;
+        uint32_t rphase = 0;
+        for (int t = blockIdx.x; ok; t += gridDim.x) {
+            if (CHAIN) {
+                if (!mbar_wait(&rfull[ri], rphase, abort_flag, status0, kWaitTimeoutNs))
+                    break;
+                t = tring[ri];
+                mbar_arrive(&rempty[ri]);
+                if (++ri == kRingTiles) {
+                    ri = 0;
+                    rphase ^= 1u;
+                }
+                if (t < 0)
+                    break;
+            } else if (t >= total) {
+                break;
+            }
             TileCoord tc = decode_tile<BN>(L, t);
             if (!tc.valid)
                 continue;
@@ -747,11 +833,37 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         int last_prob = -1;
         EpiScales sc{1.f, 0.f, 0.f};
         EpiOverride ov{nullptr, 0, nullptr, 0, 0};
-        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int ri = 0;
+        uint32_t rphase = 0;
+        for (int t = blockIdx.x;; t += gridDim.x) {
+            if (CHAIN) {
+                if (!mbar_wait(&rfull[ri], rphase, abort_flag, status0, kWaitTimeoutNs))
+                    break;
+                t = tring[ri];
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&rempty[ri]);
+                if (++ri == kRingTiles) {
+                    ri = 0;
+                    rphase ^= 1u;
+                }
+                if (t < 0)
+                    break;
+            } else if (t >= total) {
+                break;
+            }
             TileCoord tc = decode_tile<BN>(L, t);
             if (!tc.valid)
                 continue;
             const TcProblem &P = prob_at(L, tc.prob);
+            if (CHAIN && (P.ep.c_kind != C_NONE || P.ep.theta_src)) {
+                // C or the norm bound is an earlier result: make it visible to these loads.
+                for (int d = 0; d < 2; ++d)
+                    if (P.dep[d] >= 0 && lane == 0)
+                        wait_counter(&L.done[P.dep[d]], P.dep_target[d], abort_flag, status0,
+                                     kWaitTimeoutNs);
+                __syncwarp();
+            }
             if (tc.prob != last_prob) {
                 ov.c0 = P.ep.c0;
                 ov.ldc = P.ep.ldc;
@@ -759,8 +871,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 ov.ldo = P.ep.ldo;
                 ov.otma = P.o_tma;
                 double alpha = P.ep.alpha;
-                if (P.patch && L.calls) {  // grouped launch: per-call fields
-                    const CallRec &cr = L.calls[P.call_idx];
+                if (P.patch) {  // grouped / fused launch: per-call fields
+                    const CallRec &cr = calls[P.call_idx];
                     if (P.patch & PT_C_IS_A) {
                         ov.c0 = cr.A;
                         ov.ldc = cr.lda;
@@ -806,6 +918,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 buf = 0;
                 tphase ^= 1u;
             }
+            if (CHAIN) {
+                // Publish: this warp's part of the tile is in global memory.
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) {
+                    bulk_wait_all0();
+                    fence_async_global();
+                    __threadfence();
+                    atomicAdd(&L.done[P.pid], 1);
+                }
+                __syncwarp();
+            }
         }
         // All TMA stores of this warp complete before the CTA may exit.
         if (lane == 0)
@@ -827,7 +951,7 @@ template <int BN, int STAGES>
 constexpr int smem_bytes()
 {
     return STAGES * (kBM + BN) * kBK * 2 + kEpiWarps * 4096 /* epilogue staging */ +
-           1024 /* alignment slack */ + 256 /* barriers */;
+           1024 /* alignment slack */ + 512 /* barriers, tile ring */;
 }
 
 template <int BN, int STAGES>
@@ -836,7 +960,7 @@ cudaError_t launch_bn(const TcLaunch &l, int num_sms, cudaStream_t s)
     static bool configured = false;
     constexpr int smem = smem_bytes<BN, STAGES>();
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess)
             return e;
@@ -848,7 +972,22 @@ cudaError_t launch_bn(const TcLaunch &l, int num_sms, cudaStream_t s)
     if (total < 0)
         total = num_sms;  // grouped launch: the tile count lives on the device
     int grid = total < num_sms ? total : num_sms;
-    tc_gemm_kernel<BN, STAGES><<<grid, kThreads, smem, s>>>(l);
+    tc_gemm_kernel<BN, STAGES, false><<<grid, kThreads, smem, s>>>(l);
+    return cudaGetLastError();
+}
+
+template <int BN, int STAGES, bool CHAIN>
+cudaError_t launch_table(const TcLaunch &l, int total_tiles, int num_sms, cudaStream_t s)
+{
+    constexpr int smem = smem_bytes<BN, STAGES>();
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, CHAIN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess)
+        return e;
+    if (total_tiles <= 0)
+        return cudaSuccess;
+    const int grid = total_tiles < num_sms ? total_tiles : num_sms;
+    tc_gemm_kernel<BN, STAGES, CHAIN><<<grid, kThreads, smem, s>>>(l);
     return cudaGetLastError();
 }
 
@@ -857,28 +996,25 @@ cudaError_t launch_bn(const TcLaunch &l, int num_sms, cudaStream_t s)
 cudaError_t tc_gemm_launch_grouped(const TcLaunch &l, int bn, int total_tiles, int num_sms,
                                    cudaStream_t s)
 {
-    if (total_tiles <= 0)
-        return cudaSuccess;
     TcLaunch g = l;
     g.nprob = 0;
-    if (bn == 256) {
-        constexpr int smem = smem_bytes<256, 4>();
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<256, 4>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess)
-            return e;
-        tc_gemm_kernel<256, 4><<<total_tiles < num_sms ? total_tiles : num_sms, kThreads, smem, s>>>(g);
-    } else if (bn == 128) {
-        constexpr int smem = smem_bytes<128, 6>();
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<128, 6>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess)
-            return e;
-        tc_gemm_kernel<128, 6><<<total_tiles < num_sms ? total_tiles : num_sms, kThreads, smem, s>>>(g);
-    } else {
-        return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    if (bn == 256)
+        return launch_table<256, 4, false>(g, total_tiles, num_sms, s);
+    if (bn == 128)
+        return launch_table<128, 6, false>(g, total_tiles, num_sms, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t tc_gemm_launch_fused(const TcLaunch &l, int bn, int total_tiles, int num_sms,
+                                 cudaStream_t s)
+{
+    TcLaunch g = l;
+    g.nprob = 0;
+    if (bn == 256)
+        return launch_table<256, 4, true>(g, total_tiles, num_sms, s);
+    if (bn == 128)
+        return launch_table<128, 6, true>(g, total_tiles, num_sms, s);
+    return cudaErrorInvalidValue;
 }
 
 int tc_num_tiles(const TcProblem &p, int bn)

@@ -34,6 +34,7 @@ struct Resolved {
     int polish;
     int mode;
     int hp_steps;   // leading S-chain steps in the FP32-class tier (BF16 tier)
+    int fuse;       // one persistent launch for all products of a solve
 };
 
 bool resolve(const svt_options *in, Resolved *r);
@@ -48,7 +49,9 @@ struct Buf {
 struct Layout {
     int64_t M = 0, N = 0, ldM = 0, ldN = 0;
     size_t esz = 2;          // element size of matrix buffers (2 BF16, 8 FP64)
-    size_t scal = 0, status = 0, colnorm = 0;
+    size_t scal = 0, status = 0, counters = 0, colnorm = 0;
+    int max_problems = 0;    // capacity of the fused counters / table
+    size_t fused_tab = 0, fused_tab_bytes = 0;
     Buf X[2], Xt[2], XtLo0, S[2], Yp, Zp, Ys, Zs, ZPp, ZSp, B, Sp;
     size_t total = 0;
 };
@@ -85,6 +88,21 @@ struct Plan {
     std::vector<F64Launch> f64;
     std::vector<PatchRec> patches;
     std::vector<double> tc_flops;   // algorithmic flops of each tensor-core launch
+    std::vector<int> tc_chain;      // per problem of each launch: 0 P chain, 1 S chain, 2 both
+    // Fused execution: one launch for every product (table and counters in the workspace).
+    bool fused = false;
+    TcLaunch fused_launch;
+    int fused_tiles = 0, fused_bn = 0;
+    double fused_flops = 0.0;
+    // The fused table lives in the shared workspace, which other solves overwrite:
+    // it is copied from this immutable pinned host image before every fused launch.
+    uint8_t *h_fused = nullptr;
+    size_t fused_bytes = 0;
+    ~Plan()
+    {
+        if (h_fused)
+            cudaFreeHost(h_fused);
+    }
     int tc_launches_per_solve = 0;
     int kernel_launches = 0;
     int force_bn = 0;               // 0: tile width per launch; 128 / 256: fixed (grouped batches);
@@ -116,12 +134,13 @@ struct Key {
     double ell0, delta;
     size_t ws_base;
     int force_bn;
+    int fuse;
     bool operator<(const Key &o) const
     {
         return std::tie(m, n, iters, prec, schedule, norm, polish, mode, hp_steps, ell0, delta,
-                        ws_base, force_bn) < std::tie(o.m, o.n, o.iters, o.prec, o.schedule,
-                                                      o.norm, o.polish, o.mode, o.hp_steps,
-                                                      o.ell0, o.delta, o.ws_base, o.force_bn);
+                        ws_base, force_bn, fuse) <
+               std::tie(o.m, o.n, o.iters, o.prec, o.schedule, o.norm, o.polish, o.mode,
+                        o.hp_steps, o.ell0, o.delta, o.ws_base, o.force_bn, o.fuse);
     }
 };
 
@@ -159,6 +178,9 @@ struct svt_ctx {
     std::vector<ProfRec> prof_pending;
     size_t prof_next = 0;
     std::map<svt::TuneKey, std::vector<int>> tuning;  // svt_autotune results
+    // Which grouped-batch plan's device tables are intact in the workspace (any
+    // other use of the workspace resets it; the batch then re-uploads its tables).
+    const void *table_owner = nullptr;
 };
 
 namespace svt {

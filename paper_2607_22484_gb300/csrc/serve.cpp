@@ -133,6 +133,9 @@ struct BatchPlan {
     cudaEvent_t uploaded = nullptr;  // the previous replay consumed h_calls
     bool pending = false;
     int kernels_per_call = 0;
+    // Host images of the device tables, re-uploaded when another user of the
+    // workspace has overwritten them since this plan last ran.
+    std::vector<std::pair<void *, std::vector<uint8_t>>> tables;
     ~BatchPlan()
     {
         if (exec)
@@ -272,6 +275,7 @@ svt_status issue_window(svt_ctx *ctx, ServeState *s)
             return SVT_ERR_CUDA;
         s->ring_busy[k] = false;
     }
+    ctx->table_owner = nullptr;
     uint8_t *h = s->h_ring + (size_t)k * kRingSlotBytes;
     uint8_t *d = ctx->ws + (ctx->ws_bytes - kRingBytes) + (size_t)k * kRingSlotBytes;
     size_t used = 0;
@@ -581,9 +585,11 @@ void scheduler(svt_ctx *ctx, ServeState *s)
 // Merge the per-matrix plans stage by stage into grouped launches, upload the
 // device tables and capture the launch sequence in a CUDA graph.
 svt_status build_batch(svt_ctx *ctx, ServeState *s, const svt_matrix *mats, int count,
-                       const Resolved &r, const std::vector<size_t> &off, size_t tables_off,
+                       const Resolved &r_in, const std::vector<size_t> &off, size_t tables_off,
                        int bn, BatchPlan *bp)
 {
+    Resolved r = r_in;
+    r.fuse = 0;  // grouped launches take the per-stage problems
     std::vector<Plan *> plans(count);
     for (int i = 0; i < count; ++i) {
         svt_status st = get_plan(ctx, mats[i].m, mats[i].n, r, off[i], ctx->ws_bytes - off[i],
@@ -653,9 +659,9 @@ svt_status build_batch(svt_ctx *ctx, ServeState *s, const svt_matrix *mats, int 
     bp->blocks_split = blk_s;
     bp->d_aux = reinterpret_cast<AuxRec *>(tbase + take(sizeof(AuxRec) * count));
     bp->d_calls = reinterpret_cast<CallRec *>(tbase + take(sizeof(CallRec) * count));
-    if (cudaMemcpy(bp->d_aux, aux.data(), sizeof(AuxRec) * count, cudaMemcpyHostToDevice) !=
-        cudaSuccess)
-        return SVT_ERR_CUDA;
+    bp->tables.emplace_back(bp->d_aux, std::vector<uint8_t>(
+                                           reinterpret_cast<uint8_t *>(aux.data()),
+                                           reinterpret_cast<uint8_t *>(aux.data() + count)));
     // Grouped product launches: op k of every matrix.
     std::vector<TcProblem> probs;
     std::vector<int> starts;
@@ -688,11 +694,12 @@ svt_status build_batch(svt_ctx *ctx, ServeState *s, const svt_matrix *mats, int 
         int *ds = reinterpret_cast<int *>(tbase + take(sizeof(int) * starts.size()));
         if (toff > batch_table_bytes(count, r))
             return SVT_ERR_OOM;
-        if (cudaMemcpy(dp, probs.data(), sizeof(TcProblem) * probs.size(), cudaMemcpyHostToDevice) !=
-                cudaSuccess ||
-            cudaMemcpy(ds, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice) !=
-                cudaSuccess)
-            return SVT_ERR_CUDA;
+        bp->tables.emplace_back(dp, std::vector<uint8_t>(
+                                        reinterpret_cast<uint8_t *>(probs.data()),
+                                        reinterpret_cast<uint8_t *>(probs.data() + probs.size())));
+        bp->tables.emplace_back(ds, std::vector<uint8_t>(
+                                        reinterpret_cast<uint8_t *>(starts.data()),
+                                        reinterpret_cast<uint8_t *>(starts.data() + starts.size())));
         TcLaunch L;
         std::memset(&L, 0, sizeof(L));
         L.gtab = dp;
@@ -916,6 +923,13 @@ svt_status svt_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, void *str
         if (bp) {
             if (bp->pending && cudaEventSynchronize(bp->uploaded) != cudaSuccess)
                 return SVT_ERR_CUDA;
+            if (ctx->table_owner != bp) {
+                for (auto &t : bp->tables)
+                    if (cudaMemcpyAsync(t.first, t.second.data(), t.second.size(),
+                                        cudaMemcpyHostToDevice, cs) != cudaSuccess)
+                        return SVT_ERR_CUDA;
+                ctx->table_owner = bp;
+            }
             for (int i = 0; i < count; ++i) {
                 CallRec &c = bp->h_calls[i];
                 c.A = mats[i].A;
@@ -971,6 +985,7 @@ svt_status svt_serve_submit(svt_ctx_t ctx, const svt_matrix *req, uint64_t *tick
     Resolved r;
     if (!resolve(&req->opt, &r))
         return SVT_ERR_INVALID;
+    r.fuse = 0;  // serving windows group per-stage problems across requests
     if (r.prec == SVT_FP64 && (req->m > kF64MaxDim || req->n > kF64MaxDim))
         return SVT_ERR_UNSUPPORTED;
     size_t need = align_up(make_layout(req->m, req->n, r).total, kAlign);

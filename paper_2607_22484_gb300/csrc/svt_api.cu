@@ -152,6 +152,7 @@ bool resolve(const svt_options *in, Resolved *r)
     if (o.hp_steps < -1)
         return false;
     r->hp_steps = (o.prec == SVT_BF16) ? o.hp_steps : 0;
+    r->fuse = (o.fuse && o.prec != SVT_FP64) ? 1 : 0;
     return true;
 }
 
@@ -196,6 +197,9 @@ Layout make_layout(int64_t m, int64_t n, const Resolved &r)
     Alloc a;
     L.scal = a.take(SC_COUNT * sizeof(double));
     L.status = a.take(sizeof(int) * 4);
+    // Product launches of a solve: Gram, 3 per step, 2 polish, combine; <= 2 problems each.
+    L.max_problems = 2 * (1 + 3 * std::max(0, r.iters) + 2 + 1);
+    L.counters = a.take(sizeof(int) * (size_t)(L.max_problems + 1));  // done[], tile counter
     L.colnorm = a.take((size_t)L.N * sizeof(double));
     const bool pairs = fp32;  // iterates carried as hi/lo pairs
     for (int i = 0; i < 2; ++i) {
@@ -220,6 +224,11 @@ Layout make_layout(int64_t m, int64_t n, const Resolved &r)
     L.ZSp = make_buf(a, L.N, L.N, L.esz, !f64);
     L.B = make_buf(a, L.M, L.N, L.esz, !f64);
     L.Sp = make_buf(a, L.N, L.N, L.esz, !f64);
+    if (!f64 && r.fuse) {
+        L.fused_tab_bytes = align_up(sizeof(TcProblem) * (size_t)L.max_problems, kAlign) +
+                            align_up(sizeof(int) * (size_t)(L.max_problems + 1), kAlign);
+        L.fused_tab = a.take(L.fused_tab_bytes);
+    }
     L.total = a.off;
     return L;
 }
@@ -329,6 +338,7 @@ struct Builder {
         bool sym;
         Epi e;
         int patch;
+        int chain = 0;  // 0 P chain, 1 S chain, 2 both (combine)
     };
 
     bool emit(const std::vector<Prod> &prods)
@@ -366,6 +376,7 @@ struct Builder {
             const Prod &q = prods[i];
             if (!tc_problem(l.p[i], *q.L, *q.R, q.M, q.N, q.K, q.sym, q.e, bn))
                 return false;
+            plan->tc_chain.push_back(q.chain);
             l.tile_start[i] = start;
             start += tc_num_tiles(l.p[i], bn);
             if (q.patch)
@@ -440,7 +451,7 @@ struct Builder {
             e.diag = reinterpret_cast<const double *>(base + L.colnorm);
             e.dss = scal(SC_INV_ALPHA2);  // [INV_ALPHA2, TAU2_SCALED]
             e.norm_acc = scal(SC_NRM_S0);
-            if (!emit({{&Lg, &Lg, N, N, M, true, e, 0}}))
+            if (!emit({{&Lg, &Lg, N, N, M, true, e, 0, 1}}))
                 return false;
         }
 
@@ -490,7 +501,7 @@ struct Builder {
                     set_out(e, L.Ys, hp);
                     if (first && o.norm == SVT_NORM_GRAM)
                         e.norm_acc = scal(SC_NRM_YS);
-                    s1.push_back({&Sc, &Sc, N, N, N, true, e, 0});
+                    s1.push_back({&Sc, &Sc, N, N, N, true, e, 0, 1});
                 }
                 if (!emit(s1))
                     return false;
@@ -512,7 +523,7 @@ struct Builder {
                     set_c(e, Ysv, b);
                     set_out(e, L.Zs, hp);
                     theta(e, thS, powS, 5, 3, 1);
-                    s2.push_back({&Ysv, &Ysv, N, N, N, true, e, 0});
+                    s2.push_back({&Ysv, &Ysv, N, N, N, true, e, 0, 1});
                 }
                 if (!emit(s2))
                     return false;
@@ -533,7 +544,7 @@ struct Builder {
                     e.gamma = a;
                     set_out(e, L.Zs, hp);
                     theta(e, thS, powS, 3, 0, 1);
-                    s1.push_back({&Sc, &Sc, N, N, N, true, e, 0});
+                    s1.push_back({&Sc, &Sc, N, N, N, true, e, 0, 1});
                 }
                 if (!emit(s1))
                     return false;
@@ -549,7 +560,7 @@ struct Builder {
             {
                 Epi e = epi0();
                 set_out(e, L.S[nxt], s_pair(t + 1));
-                s3.push_back({&Sc, &Zsv, N, N, N, true, e, 0});
+                s3.push_back({&Sc, &Zsv, N, N, N, true, e, 0, 1});
             }
             if (!emit(s3))
                 return false;
@@ -572,7 +583,7 @@ struct Builder {
                 e.alpha = -0.5;
                 e.gamma = 1.5;
                 set_out(e, L.ZSp, !f64);
-                s1.push_back({&Sfin, &Sfin, N, N, N, true, e, 0});
+                s1.push_back({&Sfin, &Sfin, N, N, N, true, e, 0, 1});
             }
             if (!emit(s1))
                 return false;
@@ -589,7 +600,7 @@ struct Builder {
             {
                 Epi e = epi0();
                 set_out(e, L.Sp, !f64);
-                s2.push_back({&Sfin, &L.ZSp, N, N, N, true, e, 0});
+                s2.push_back({&Sfin, &L.ZSp, N, N, N, true, e, 0, 1});
             }
             if (!emit(s2))
                 return false;
@@ -610,7 +621,7 @@ struct Builder {
             e.o_kind = f64 ? O_F32 : O_F32;
             e.o_trans = P.wide ? 1 : 0;
             e.norm_acc = scal(SC_NRM_OUT);
-            if (!emit({{&L.B, &L.Sp, M, N, N, false, e, PT_O_IS_Y}}))
+            if (!emit({{&L.B, &L.Sp, M, N, N, false, e, PT_O_IS_Y, 2}}))
                 return false;
         }
         P.ops.push_back({OP_FINAL, 0, 0});
@@ -680,8 +691,50 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
     cudaError_t err = cudaSuccess;
     int cur_final = P.opt.iters % 2;
     int launched = 0;
+    const bool fused = P.fused && first == 0 && last >= P.ops.size();
+    bool fused_done = false;
+    ctx->table_owner = nullptr;  // this solve overwrites part of the workspace
     for (size_t oi = first; oi < last && oi < P.ops.size(); ++oi) {
         const Op &op = P.ops[oi];
+        if (fused && op.kind == OP_TC) {
+            if (fused_done)
+                continue;
+            fused_done = true;
+            // The table region is shared with other plans: refresh it from the host image.
+            if (cudaMemcpyAsync(const_cast<TcProblem *>(P.fused_launch.gtab), P.h_fused,
+                                P.fused_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return SVT_ERR_CUDA;
+            TcLaunch l = P.fused_launch;
+            l.call_inline.A = a.A;
+            l.call_inline.Y = a.Y;
+            l.call_inline.lda = a.lda;
+            l.call_inline.ldy = a.ldy;
+            l.call_inline.tau = a.tau;
+            l.call_inline.d_status = a.d_status;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (ctx->profile) {
+                if (ctx->prof_next + 2 > ctx->prof_pool.size()) {
+                    for (int k = 0; k < 64; ++k) {
+                        cudaEvent_t ev;
+                        if (cudaEventCreate(&ev) != cudaSuccess)
+                            return SVT_ERR_CUDA;
+                        ctx->prof_pool.push_back(ev);
+                    }
+                }
+                e0 = ctx->prof_pool[ctx->prof_next++];
+                e1 = ctx->prof_pool[ctx->prof_next++];
+                cudaEventRecord(e0, s);
+            }
+            err = tc_gemm_launch_fused(l, P.fused_bn, P.fused_tiles, ctx->num_sms, s);
+            if (ctx->profile) {
+                cudaEventRecord(e1, s);
+                ctx->prof_pending.push_back({e0, e1, P.fused_flops});
+            }
+            ++launched;
+            if (err != cudaSuccess)
+                return SVT_ERR_CUDA;
+            continue;
+        }
         if (op.kind != OP_MEMSET)
             ++launched;
         switch (op.kind) {
@@ -798,6 +851,115 @@ svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s)
     return run_ops(ctx, P, a, s, 0, P.ops.size());
 }
 
+namespace {
+
+int valid_tiles(const TcProblem &p, int bn)
+{
+    if (!p.sym)
+        return p.tiles_m * p.tiles_n;
+    const int r = bn / kBM;
+    int n = 0;
+    for (int tn = 0; tn < p.tiles_n; ++tn)
+        n += std::min(r * (tn + 1), p.tiles_m);
+    return n;
+}
+
+// One persistent launch for all products of the plan: problems in program order,
+// each depending on the previous problem of its chain (the combine on both chains).
+// Eligible when the products are contiguous in the op list and share one tile width.
+svt_status build_fused(svt_ctx *ctx, Plan &P)
+{
+    P.fused = false;
+    if (!P.lay.fused_tab_bytes)
+        return SVT_OK;
+    size_t first = P.ops.size(), last = 0;
+    int bn = 0;
+    for (size_t i = 0; i < P.ops.size(); ++i) {
+        if (P.ops[i].kind != OP_TC)
+            continue;
+        first = std::min(first, i);
+        last = i;
+        if (bn && P.ops[i].bn != bn)
+            return SVT_OK;
+        bn = P.ops[i].bn;
+    }
+    if (first > last)
+        return SVT_OK;
+    for (size_t i = first; i <= last; ++i)
+        if (P.ops[i].kind != OP_TC)
+            return SVT_OK;
+    std::vector<TcProblem> probs;
+    std::vector<int> starts, valid;
+    int lastp[2] = {-1, -1};
+    size_t ci = 0;
+    int total = 0;
+    for (size_t i = first; i <= last; ++i) {
+        const int li = P.ops[i].idx;
+        const TcLaunch &l = P.tc[li];
+        for (int q = 0; q < l.nprob; ++q) {
+            TcProblem tp = l.p[q];
+            const int chain = P.tc_chain[ci++];
+            tp.pid = (int)probs.size();
+            tp.dep[0] = tp.dep[1] = -1;
+            tp.dep_target[0] = tp.dep_target[1] = 0;
+            tp.patch = 0;
+            tp.call_idx = 0;
+            for (const PatchRec &pr : P.patches)
+                if (pr.kind == OP_TC && pr.launch == li && pr.prob == q)
+                    tp.patch |= pr.flags;
+            if (tp.patch & PT_O_IS_Y)
+                tp.o_tma = 0;  // the caller's output: plain coalesced stores
+            if (chain < 2) {
+                tp.dep[0] = lastp[chain];
+            } else {
+                tp.dep[0] = lastp[0];
+                tp.dep[1] = lastp[1];
+            }
+            for (int d = 0; d < 2; ++d)
+                if (tp.dep[d] >= 0)
+                    tp.dep_target[d] = kEpiWarpsPublic * valid[tp.dep[d]];
+            starts.push_back(total);
+            total += tc_num_tiles(tp, bn);
+            valid.push_back(valid_tiles(tp, bn));
+            if (chain < 2)
+                lastp[chain] = tp.pid;
+            else
+                lastp[0] = lastp[1] = tp.pid;
+            probs.push_back(tp);
+        }
+    }
+    starts.push_back(total);
+    if ((int)probs.size() > P.lay.max_problems)
+        return SVT_OK;
+    uint8_t *base = ctx->ws + P.ws_base;
+    const size_t tab_bytes = align_up(sizeof(TcProblem) * (size_t)P.lay.max_problems, kAlign);
+    TcProblem *dp = reinterpret_cast<TcProblem *>(base + P.lay.fused_tab);
+    int *ds = reinterpret_cast<int *>(base + P.lay.fused_tab + tab_bytes);
+    // Pinned host image of [problems | starts], copied to the device at every call.
+    P.fused_bytes = tab_bytes + sizeof(int) * starts.size();
+    if (cudaMallocHost(reinterpret_cast<void **>(&P.h_fused), P.fused_bytes) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    std::memset(P.h_fused, 0, P.fused_bytes);
+    std::memcpy(P.h_fused, probs.data(), sizeof(TcProblem) * probs.size());
+    std::memcpy(P.h_fused + tab_bytes, starts.data(), sizeof(int) * starts.size());
+    std::memset(&P.fused_launch, 0, sizeof(P.fused_launch));
+    P.fused_launch.gtab = dp;
+    P.fused_launch.gstart = ds;
+    P.fused_launch.gcount = (int)probs.size();
+    int *counters = reinterpret_cast<int *>(base + P.lay.counters);
+    P.fused_launch.done = counters;
+    P.fused_launch.tile_counter = counters + P.lay.max_problems;
+    P.fused_tiles = total;
+    P.fused_bn = bn;
+    P.fused_flops = 0.0;
+    for (double f : P.tc_flops)
+        P.fused_flops += f;
+    P.fused = true;
+    return SVT_OK;
+}
+
+} // namespace
+
 void evict_plans(svt_ctx *ctx, size_t max_entries)
 {
     if (ctx->plans.size() <= max_entries)
@@ -814,7 +976,7 @@ svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_
                     size_t ws_avail, Plan **out, int force_bn, std::shared_ptr<Plan> *keep)
 {
     Key k{m, n, r.iters, r.prec, r.schedule, r.norm, r.polish, r.mode, r.hp_steps, r.ell0, r.delta,
-          ws_base, force_bn};
+          ws_base, force_bn, r.fuse};
     auto it = ctx->plans.find(k);
     if (it != ctx->plans.end()) {
         *out = it->second.get();
@@ -845,6 +1007,8 @@ svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_
         return SVT_ERR_INVALID;
     Builder b{ctx, plan.get(), ctx->ws + ws_base, 256};
     if (!b.build())
+        return SVT_ERR_CUDA;
+    if (r.fuse && build_fused(ctx, *plan) != SVT_OK)
         return SVT_ERR_CUDA;
     *out = plan.get();
     if (keep)
@@ -916,6 +1080,7 @@ void svt_options_default(svt_options *o)
     o->polish = 1;
     o->mode = SVT_MODE_SVT;
     o->hp_steps = -1;
+    o->fuse = 1;
 }
 
 svt_status svt_workspace_bytes_ex(int64_t m, int64_t n, const svt_options *opt, size_t *out)
@@ -1029,11 +1194,13 @@ svt_status svt_autotune(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CallArgs a{A, lda, tau, Y, ldy, nullptr};
     const int widths[2] = {128, 256};
+    Resolved rt = r;
+    rt.fuse = 0;  // launch-by-launch timing needs the unfused plan
     std::vector<double> ms[2];
     const bool prev_profile = ctx->profile;
     for (int w = 0; w < 2; ++w) {
         Plan *plan = nullptr;
-        st = get_plan(ctx, m, n, r, 0, ctx->ws_bytes, &plan, widths[w]);
+        st = get_plan(ctx, m, n, rt, 0, ctx->ws_bytes, &plan, widths[w]);
         if (st != SVT_OK)
             return st;
         st = run_plan(ctx, *plan, a, s);  // warm-up

@@ -83,6 +83,11 @@ struct TcProblem {
     CUtensorMap mapT[2];             // transposed copy hi/lo, box 32 x 32
     int o_tma, t_tma;                // 1: store through mapO / mapT
     int patch, call_idx;             // grouped launches: fields taken from calls[call_idx]
+    // Fused (chained) launches: completion counter index of this problem, and the
+    // problems whose results it reads with the counts that mean "complete".
+    int pid;
+    int dep[2];
+    int dep_target[2];
     int nseg;
     int segL[3], segR[3];
     int M, N, K;
@@ -100,6 +105,12 @@ struct TcLaunch {
     const int *gstart;               // gcount + 1 entries
     int gcount;
     const CallRec *calls;
+    // Fused launch (all products of a solve, device-side dependencies): tiles are
+    // taken in table order from *tile_counter; done[pid] counts finished
+    // (tile, epilogue warp) pairs. Both live in the solve's zeroed scratch.
+    int *tile_counter;
+    int *done;
+    CallRec call_inline;             // per-call fields when calls == nullptr
 };
 
 // One product of the FP64 SIMT path: D = L R^T, L M x K (ldl), R N x K (ldr).
@@ -123,6 +134,11 @@ cudaError_t tc_gemm_launch(const TcLaunch &l, int bn, int num_sms, cudaStream_t 
 // total_tiles (host copy of gstart[gcount]) sizes the grid.
 cudaError_t tc_gemm_launch_grouped(const TcLaunch &l, int bn, int total_tiles, int num_sms,
                                    cudaStream_t s);
+// Fused launch: l.gtab / l.gstart / l.gcount hold every product of a solve in
+// dependency order; l.tile_counter and l.done point to zeroed device counters.
+cudaError_t tc_gemm_launch_fused(const TcLaunch &l, int bn, int total_tiles, int num_sms,
+                                 cudaStream_t s);
+constexpr int kEpiWarpsPublic = 8;  // completion count per tile of a fused launch
 cudaError_t f64_gemm_launch(const F64Launch &l, cudaStream_t s);
 
 // Ingest: FP64 column norms of the tall matrix and ||A||_F^2.

@@ -169,3 +169,17 @@ def test_autotuned_plan_matches_oracle(ctx):
     y = ctx.polar(dev, 0.3, iters=20, prec="bf16")
     torch.cuda.synchronize()
     assert oracle.relerr(y.cpu().numpy(), exact) < 2e-2
+
+
+@pytest.mark.parametrize("prec,shape", [("bf16", (520, 384)), ("fp32", (300, 700)), ("bf16", (1024, 1024))])
+def test_fused_launch_matches_separate_launches(ctx, prec, shape):
+    """All products in one persistent launch with device-side dependencies give the
+    same result as one launch per product stage."""
+    a = _gap_matrix(*shape, seed=shape[0] + shape[1])
+    dev = torch.from_numpy(a).cuda()
+    y1 = ctx.polar(dev, 0.3, iters=20, prec=prec, fuse=True)
+    y0 = ctx.polar(dev, 0.3, iters=20, prec=prec, fuse=False)
+    torch.cuda.synchronize()
+    assert oracle.relerr(y1.cpu().numpy(), y0.cpu().numpy()) < 1e-5
+    exact = oracle.svt_definition(a.astype(np.float64), 0.3)
+    assert oracle.relerr(y1.cpu().numpy(), exact) < TOL[prec]
