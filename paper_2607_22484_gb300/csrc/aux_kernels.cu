@@ -319,9 +319,9 @@ __global__ void __launch_bounds__(256) f64_gemm_kernel(const __grid_constant__ F
             al *= pow(theta, -e.ea);
             be *= pow(theta, -e.eb);
             ga *= pow(theta, -e.eg);
-        } else {
+        } else if (!isfinite(theta)) {
             set_status(e.status, SVT_ERR_DIVERGED);
-        }
+        }  // theta == 0: the chain's matrix is zero; nothing to scale
     }
     double nrm = 0.0;
 #pragma unroll

@@ -294,21 +294,28 @@ __device__ __forceinline__ EpiScales epi_scales(const Epi &e, double alpha)
             s.alpha = (float)(alpha * pow(theta, -e.ea));
             s.beta = (float)(e.beta * pow(theta, -e.eb));
             s.gamma = (float)(e.gamma * pow(theta, -e.eg));
-        } else if (e.status) {
+        } else if (!isfinite(theta) && e.status) {
             atomicCAS(e.status, 0, (int)SVT_ERR_DIVERGED);
-        }
+        }  // theta == 0: the chain's matrix is zero; nothing to scale
     }
     return s;
 }
 
+__device__ __forceinline__ bool aligned16(const void *p)
+{
+    return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
 // v[i] += beta * C(r, c0 + i) for i < ncol, vectorised where the row segment is
-// contiguous and aligned.
+// contiguous and its address (not just its offset) is 16-byte aligned.
 __device__ __forceinline__ void add_c32(const Epi &e, const void *cp0, int64_t ldc, int64_t r,
                                         int64_t c0, int ncol, float beta, float *v)
 {
     if (!e.c_trans) {
         const int64_t off = r * ldc + c0;
-        if (ncol == 32 && (e.c_kind == C_BF16 || e.c_kind == C_PAIR) && (off & 7) == 0) {
+        if (ncol == 32 && (e.c_kind == C_BF16 || e.c_kind == C_PAIR) &&
+            aligned16(static_cast<const __nv_bfloat16 *>(cp0) + off) &&
+            (e.c_kind == C_BF16 || aligned16(static_cast<const __nv_bfloat16 *>(e.c1) + off))) {
             const uint4 *h = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(cp0) + off);
             const uint4 *l = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(e.c1) + off);
 #pragma unroll
@@ -334,7 +341,7 @@ __device__ __forceinline__ void add_c32(const Epi &e, const void *cp0, int64_t l
             }
             return;
         }
-        if (ncol == 32 && e.c_kind == C_F32 && (off & 3) == 0) {
+        if (ncol == 32 && e.c_kind == C_F32 && aligned16(static_cast<const float *>(cp0) + off)) {
             const float4 *f = reinterpret_cast<const float4 *>(static_cast<const float *>(cp0) + off);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -403,7 +410,8 @@ __device__ __forceinline__ void store_block(const float *st, int kind, void *p0,
                 continue;
             const int64_t C = ocol0 + q * 8;
             const int64_t off = R * ld + C;
-            if (C + 8 <= ocols && (off & 7) == 0) {
+            if (C + 8 <= ocols && aligned16(static_cast<__nv_bfloat16 *>(p0) + off) &&
+                (kind != O_PAIR || aligned16(static_cast<__nv_bfloat16 *>(p1) + off))) {
                 uint32_t hw[4], lw[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -451,7 +459,7 @@ __device__ __forceinline__ void store_block(const float *st, int kind, void *p0,
                 continue;
             const int64_t C = ocol0 + q * 4;
             const int64_t off = R * ld + C;
-            if (C + 4 <= ocols && (off & 3) == 0) {
+            if (C + 4 <= ocols && aligned16(static_cast<float *>(p0) + off)) {
                 *reinterpret_cast<float4 *>(static_cast<float *>(p0) + off) =
                     make_float4(x[0], x[1], x[2], x[3]);
             } else {

@@ -1,0 +1,98 @@
+"""Edge cases of the GPU solve through the C ABI: vectors and tiny matrices, the zero
+matrix, tau on a singular value, strided input/output, and argument limits."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+pkg = pytest.importorskip("paper_2607_22484_gb300")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return pkg.Context(0, workspace_bytes=16 << 20)
+
+
+def _solve(ctx, a, tau, **opts):
+    dev = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    y = ctx.polar(dev, tau, status=st, **opts)
+    torch.cuda.synchronize()
+    return y.cpu().numpy().astype(np.float64), int(st.item())
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (9, 1), (2, 3), (3, 3), (65, 1)])
+@pytest.mark.parametrize("prec", ["bf16", "fp32", "fp64"])
+def test_tiny_and_vector_shapes(ctx, shape, prec):
+    rng = np.random.default_rng(sum(shape))
+    a = rng.standard_normal(shape)
+    s = np.linalg.svd(a, compute_uv=False)
+    # tau strictly inside the widest gap of the spectrum (or below sigma_max for rank 1)
+    cand = np.concatenate([[0.0], np.sort(s)])
+    i = int(np.argmax(np.diff(cand)))
+    tau = 0.5 * (cand[i] + cand[i + 1])
+    exact, (u, sig, v) = oracle.svt_definition(a.astype(np.float32).astype(np.float64), tau,
+                                               return_svd=True)
+    y, st = _solve(ctx, a, tau, iters=30, prec=prec, schedule="ns3" if prec == "fp64" else "pe5")
+    assert st == 0
+    if oracle.gap(sig, tau) >= 0.05:
+        tol = {"bf16": 2e-2, "fp32": 1e-4, "fp64": 1e-6}[prec]
+        assert oracle.relerr(y, exact, a) < tol
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32", "fp64"])
+def test_zero_matrix(ctx, prec):
+    y, st = _solve(ctx, np.zeros((40, 24)), 0.3, iters=10, prec=prec)
+    assert st == 0
+    assert np.all(y == 0)
+
+
+def test_tau_on_a_singular_value(ctx):
+    """sigma = tau contributes (sigma - tau) = 0 either way: the result stays finite
+    and equals the SVT of the other singular values."""
+    rng = np.random.default_rng(3)
+    q1 = np.linalg.qr(rng.standard_normal((32, 32)))[0]
+    q2 = np.linalg.qr(rng.standard_normal((32, 32)))[0]
+    sig = np.concatenate([[1.0, 0.8], np.full(1, 0.5), np.linspace(0.2, 0.01, 29)])
+    a = (q1 * sig) @ q2.T
+    y, st = _solve(ctx, a, 0.5, iters=30, prec="fp32")
+    assert st == 0 and np.all(np.isfinite(y))
+    exact = (q1 * np.maximum(sig - 0.5, 0)) @ q2.T
+    # the sigma = tau term's eigenvalue of the shifted Gram is 0: the odd iteration keeps
+    # it at 0, so its weight is 1/2 (sigma - tau) = 0 -- the error stays small
+    assert oracle.relerr(y, exact) < 1e-3
+
+
+def test_strided_input_and_output(ctx):
+    rng = np.random.default_rng(8)
+    m, n = 150, 110
+    base = torch.from_numpy(rng.standard_normal((m, n + 13)).astype(np.float32)).cuda()
+    A = base[:, 5:5 + n]  # lda = n + 13, unaligned start
+    outbase = torch.full((m, n + 7), 7.0, device="cuda")
+    Y = outbase[:, 3:3 + n]
+    s = np.linalg.svd(A.cpu().numpy().astype(np.float64), compute_uv=False)
+    tau = float(np.median(s))
+    ctx.polar(A, tau, out=Y, iters=20, prec="fp32")
+    torch.cuda.synchronize()
+    exact = oracle.svt_definition(A.cpu().numpy().astype(np.float64), tau)
+    assert oracle.relerr(Y.cpu().numpy(), exact) < 1e-3  # no gap guarantee: loose
+    # columns outside Y untouched
+    ob = outbase.cpu().numpy()
+    assert np.all(ob[:, :3] == 7.0) and np.all(ob[:, 3 + n:] == 7.0)
+
+
+def test_argument_limits(ctx):
+    a = torch.zeros(8, 8, device="cuda")
+    with pytest.raises(pkg.SVTError) as e:
+        ctx.polar(a[:, :0], 0.1)
+    assert e.value.status == pkg.binding.ERR_INVALID
+    big = torch.zeros(4100, 16, device="cuda")
+    with pytest.raises(pkg.SVTError) as e:
+        ctx.polar(big, 0.1, prec="fp64")
+    assert e.value.status == pkg.binding.ERR_UNSUPPORTED
+    with pytest.raises(pkg.SVTError) as e:
+        ctx.polar(a, 0.1, ell0=1.5)
+    assert e.value.status == pkg.binding.ERR_INVALID
