@@ -246,7 +246,7 @@ def batch_extra(ctx_cls, pkg, torch, dev, steps=5, warmup=2):
             "alg_tflops": fl / (ms / 1e3) / 1e12,
             "one_at_a_time_solves_per_s": len(items) / (ms1 / 1e3),
             "speedup_vs_one_at_a_time": ms1 / ms,
-            "launches": "grouped: one product launch per stage for all matrices, CUDA graph"}
+            "launches": "one persistent product launch for all stages of all matrices (device-side dependencies), grouped ingest/finalize, CUDA graph"}
 
 
 def serving_extra(ctx_cls, pkg, torch, dev, n_req=200):

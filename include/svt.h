@@ -180,11 +180,16 @@ svt_status svt_polar_ex(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int
 
 /*
  * svt_batch: A_tau for `count` independent matrices of any sizes, enqueued on
- * `stream`. All matrices advance together: every stage of every matrix (both
- * chains) goes out as one grouped persistent launch, and the launch sequence is
- * captured once per batch shape signature into a CUDA graph and replayed.
- * The workspace must hold the sum of the matrices' workspaces
- * (svt_batch_workspace_bytes).
+ * `stream`. When all matrices share one option set with the default pipeline
+ * (BF16 or FP32 tier, polish on, SVT mode), every product of every matrix (both
+ * chains, all stages) runs as ONE persistent launch whose tiles wait on device-side
+ * counters only for the earlier products of their own matrix, between grouped
+ * ingest and finalize kernels; the sequence is captured once per batch shape
+ * signature into a CUDA graph and replayed. Other batches run as per-matrix solves
+ * over the context's worker streams. The workspace must hold the sum of the
+ * matrices' workspaces plus the launch tables (svt_batch_workspace_bytes).
+ * A second call with the same shape signature waits (on the host) until the first
+ * call's call table has been consumed.
  * Errors: as svt_polar, checked for every matrix before any launch.
  */
 svt_status svt_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, void *stream);

@@ -2,10 +2,11 @@
 //
 // svt_batch: every matrix gets its own plan at its own offset of the workspace.
 // When all matrices share one option set (the usual case), their solves are
-// merged stage by stage: each stage of every matrix -- both polar chains -- goes
-// out as ONE grouped persistent launch of the product kernel, whose problem table
-// (tensor maps included) lives in device memory, and the memory-bound steps run as
-// grouped kernels over all matrices. The whole launch sequence is captured once
+// merged into ONE persistent launch of the product kernel: its problem table
+// (tensor maps included, in device memory) lists every product of every matrix,
+// stage by stage, and each problem waits on device-side counters only for the
+// earlier products of its own matrix, so independent matrices fill each other's
+// waits. The memory-bound steps run as grouped kernels over all matrices. The whole launch sequence is captured once
 // per batch shape signature into a CUDA graph; a call uploads the per-matrix
 // pointers and thresholds (the call table) and replays the graph on the caller's
 // stream. Batches whose matrices differ in options fall back to per-matrix
@@ -26,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -133,6 +135,8 @@ struct BatchPlan {
     cudaEvent_t uploaded = nullptr;  // the previous replay consumed h_calls
     bool pending = false;
     int kernels_per_call = 0;
+    int *counters = nullptr;         // fused launch: done[] and tile counter (zeroed per call)
+    size_t counter_bytes = 0;
     // Host images of the device tables, re-uploaded when another user of the
     // workspace has overwritten them since this plan last ran.
     std::vector<std::pair<void *, std::vector<uint8_t>>> tables;
@@ -166,9 +170,20 @@ struct BatchKey {
 size_t batch_table_bytes(int count, const Resolved &r)
 {
     const size_t n_tc = 1 + 3 * (size_t)std::max(0, r.iters) + 2 + 1;
+    const size_t nprob = n_tc * 2 * (size_t)count;
     return align_up(sizeof(AuxRec) * count, kAlign) + align_up(sizeof(CallRec) * count, kAlign) +
-           n_tc * (align_up(sizeof(TcProblem) * 2 * count, kAlign) +
-                   align_up(sizeof(int) * (2 * count + 1), kAlign));
+           align_up(sizeof(TcProblem) * nprob, kAlign) + 2 * align_up(sizeof(int) * (nprob + 1), kAlign);
+}
+
+int batch_valid_tiles(const TcProblem &p, int bn)
+{
+    if (!p.sym)
+        return p.tiles_m * p.tiles_n;
+    const int r = bn / kBM;
+    int n = 0;
+    for (int tn = 0; tn < p.tiles_n; ++tn)
+        n += std::min(r * (tn + 1), p.tiles_m);
+    return n;
 }
 
 bool same_options(const Resolved &a, const Resolved &b)
@@ -662,21 +677,32 @@ svt_status build_batch(svt_ctx *ctx, ServeState *s, const svt_matrix *mats, int 
     bp->tables.emplace_back(bp->d_aux, std::vector<uint8_t>(
                                            reinterpret_cast<uint8_t *>(aux.data()),
                                            reinterpret_cast<uint8_t *>(aux.data() + count)));
-    // Grouped product launches: op k of every matrix.
+    // One persistent launch for every product of every matrix: stage-major order
+    // (stage k of all matrices, then stage k + 1), each problem depending on the
+    // previous problem of its matrix's chain (the combine on both chains).
     std::vector<TcProblem> probs;
-    std::vector<int> starts;
+    std::vector<int> starts, valid;
+    std::vector<std::array<int, 2>> lastp(count, std::array<int, 2>{-1, -1});
+    std::vector<std::vector<int>> chain_base(count);
+    for (int i = 0; i < count; ++i) {
+        const Plan &P = *plans[i];
+        int acc = 0;
+        for (const TcLaunch &l : P.tc) {
+            chain_base[i].push_back(acc);
+            acc += l.nprob;
+        }
+    }
+    int total = 0;
     for (size_t k = 0; k < p0.ops.size(); ++k) {
         if (p0.ops[k].kind != OP_TC)
             continue;
-        probs.clear();
-        starts.clear();
-        int total = 0;
         for (int i = 0; i < count; ++i) {
             const Plan &P = *plans[i];
             const int li = P.ops[k].idx;
             const TcLaunch &l = P.tc[li];
             for (int q = 0; q < l.nprob; ++q) {
                 TcProblem tp = l.p[q];
+                const int chain = P.tc_chain[chain_base[i][li] + q];
                 tp.patch = 0;
                 for (const PatchRec &pr : P.patches)
                     if (pr.kind == OP_TC && pr.launch == li && pr.prob == q)
@@ -684,31 +710,55 @@ svt_status build_batch(svt_ctx *ctx, ServeState *s, const svt_matrix *mats, int 
                 tp.call_idx = i;
                 if (tp.patch & PT_O_IS_Y)
                     tp.o_tma = 0;  // per-call output: plain stores
+                tp.pid = (int)probs.size();
+                tp.dep[0] = tp.dep[1] = -1;
+                tp.dep_target[0] = tp.dep_target[1] = 0;
+                if (chain < 2) {
+                    tp.dep[0] = lastp[i][chain];
+                } else {
+                    tp.dep[0] = lastp[i][0];
+                    tp.dep[1] = lastp[i][1];
+                }
+                for (int d = 0; d < 2; ++d)
+                    if (tp.dep[d] >= 0)
+                        tp.dep_target[d] = kEpiWarpsPublic * valid[tp.dep[d]];
                 starts.push_back(total);
                 total += tc_num_tiles(tp, bn);
+                valid.push_back(batch_valid_tiles(tp, bn));
+                if (chain < 2)
+                    lastp[i][chain] = tp.pid;
+                else
+                    lastp[i][0] = lastp[i][1] = tp.pid;
                 probs.push_back(tp);
             }
         }
-        starts.push_back(total);
-        TcProblem *dp = reinterpret_cast<TcProblem *>(tbase + take(sizeof(TcProblem) * probs.size()));
-        int *ds = reinterpret_cast<int *>(tbase + take(sizeof(int) * starts.size()));
-        if (toff > batch_table_bytes(count, r))
-            return SVT_ERR_OOM;
-        bp->tables.emplace_back(dp, std::vector<uint8_t>(
-                                        reinterpret_cast<uint8_t *>(probs.data()),
-                                        reinterpret_cast<uint8_t *>(probs.data() + probs.size())));
-        bp->tables.emplace_back(ds, std::vector<uint8_t>(
-                                        reinterpret_cast<uint8_t *>(starts.data()),
-                                        reinterpret_cast<uint8_t *>(starts.data() + starts.size())));
+    }
+    starts.push_back(total);
+    TcProblem *dp = reinterpret_cast<TcProblem *>(tbase + take(sizeof(TcProblem) * probs.size()));
+    int *ds = reinterpret_cast<int *>(tbase + take(sizeof(int) * starts.size()));
+    int *counters = reinterpret_cast<int *>(tbase + take(sizeof(int) * (probs.size() + 1)));
+    if (toff > batch_table_bytes(count, r))
+        return SVT_ERR_OOM;
+    bp->tables.emplace_back(dp, std::vector<uint8_t>(
+                                    reinterpret_cast<uint8_t *>(probs.data()),
+                                    reinterpret_cast<uint8_t *>(probs.data() + probs.size())));
+    bp->tables.emplace_back(ds, std::vector<uint8_t>(
+                                    reinterpret_cast<uint8_t *>(starts.data()),
+                                    reinterpret_cast<uint8_t *>(starts.data() + starts.size())));
+    {
         TcLaunch L;
         std::memset(&L, 0, sizeof(L));
         L.gtab = dp;
         L.gstart = ds;
         L.gcount = (int)probs.size();
         L.calls = bp->d_calls;
+        L.done = counters;
+        L.tile_counter = counters + probs.size();
         bp->launches.push_back(L);
         bp->tiles.push_back(total);
         bp->bns.push_back(bn);
+        bp->counters = counters;
+        bp->counter_bytes = sizeof(int) * (probs.size() + 1);
     }
     if (cudaMallocHost(reinterpret_cast<void **>(&bp->h_calls), sizeof(CallRec) * count) != cudaSuccess)
         return SVT_ERR_CUDA;
@@ -718,7 +768,7 @@ svt_status build_batch(svt_ctx *ctx, ServeState *s, const svt_matrix *mats, int 
     if (!s->capture && cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking) != cudaSuccess)
         return SVT_ERR_CUDA;
     for (size_t k = 0; k < bp->launches.size(); ++k)  // set function attributes before capture
-        if (tc_gemm_launch_grouped(bp->launches[k], bp->bns[k], 0, ctx->num_sms, s->capture) !=
+        if (tc_gemm_launch_fused(bp->launches[k], bp->bns[k], 0, ctx->num_sms, s->capture) !=
             cudaSuccess)
             return SVT_ERR_CUDA;
     cudaGraph_t graph = nullptr;
@@ -727,11 +777,12 @@ svt_status build_batch(svt_ctx *ctx, ServeState *s, const svt_matrix *mats, int 
         return SVT_ERR_CUDA;
     bool ok = cudaMemcpyAsync(bp->d_calls, bp->h_calls, sizeof(CallRec) * count,
                               cudaMemcpyHostToDevice, cs) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(bp->counters, 0, bp->counter_bytes, cs) == cudaSuccess;
     ok = ok && grouped_zero_launch(bp->d_aux, count, cs) == cudaSuccess;
     ok = ok && grouped_reduce_launch(bp->d_aux, bp->d_calls, count, bp->blocks_reduce, cs) == cudaSuccess;
     ok = ok && grouped_split_launch(bp->d_aux, bp->d_calls, count, bp->blocks_split, cs) == cudaSuccess;
     for (size_t k = 0; ok && k < bp->launches.size(); ++k)
-        ok = tc_gemm_launch_grouped(bp->launches[k], bp->bns[k], bp->tiles[k], ctx->num_sms, cs) ==
+        ok = tc_gemm_launch_fused(bp->launches[k], bp->bns[k], bp->tiles[k], ctx->num_sms, cs) ==
              cudaSuccess;
     ok = ok && grouped_finalize_launch(bp->d_aux, bp->d_calls, count, cs) == cudaSuccess;
     cudaError_t ec = cudaStreamEndCapture(cs, &graph);
