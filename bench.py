@@ -249,6 +249,66 @@ def batch_extra(ctx_cls, pkg, torch, dev, steps=5, warmup=2):
             "launches": "one persistent product launch for all stages of all matrices (device-side dependencies), grouped ingest/finalize, CUDA graph"}
 
 
+def completion_extra(ctx_cls, pkg, torch, dev, steps=100, svd_steps=10):
+    """Matrix completion client: M = L R^T (L, R ~ N(0,1)^{4096 x 20}, ||M||_2 ~ 10),
+    Bernoulli(0.2) mask, lambda = 0.02 ||P_Omega(M)||_2, proximal-gradient steps
+    X <- A_lambda(X + P_Omega(M - X)) through svt_prox_grad_step (BF16 tier). The
+    comparison loop thresholds with torch.linalg.svd (FP32) and runs svd_steps
+    steps (about a second each); recovery is ||X - M||_F / ||M||_F."""
+    import svt_workloads as wl
+    n = 4096
+    m_np, mask_np = wl.completion_problem(n, 20)
+    M = torch.from_numpy(m_np).to(dev)
+    W = torch.from_numpy(mask_np.astype("uint8")).to(dev)
+    Wf = W.float()
+    PM = M * Wf
+    v = torch.ones(n, device=dev) / n ** 0.5  # ||P_Omega(M)||_2 by power iteration (setup)
+    for _ in range(100):
+        v = PM.mT @ (PM @ v)
+        v = v / torch.linalg.norm(v)
+    lam = 0.02 * torch.linalg.norm(PM @ v).item()
+    ctx = ctx_cls(dev.index or 0, workspace_bytes=pkg.workspace_bytes(n, n))
+    X = torch.zeros_like(M)
+    Z = torch.empty_like(M)
+    opts = {"iters": ITERS, "prec": "bf16"}
+    for _ in range(2):
+        ctx.prox_grad_step(X, M, W, lam, Z=Z, **opts)
+    X.zero_()
+    torch.cuda.synchronize()
+    rec = lambda x: (torch.linalg.norm(x - M) / torch.linalg.norm(M)).item()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record()
+    rec_at = None
+    for k in range(steps):
+        ctx.prox_grad_step(X, M, W, lam, Z=Z, **opts)
+        if k + 1 == svd_steps:
+            e1.record()
+            torch.cuda.synchronize()
+            rec_at = rec(X)
+            ms_first = e0.elapsed_time(e1)
+            e0.record()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = ms_first + e0.elapsed_time(e1)
+    Xs = torch.zeros_like(M)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(svd_steps):
+        Zs = Xs + Wf * (M - Xs)
+        U, S, Vh = torch.linalg.svd(Zs, full_matrices=False)
+        Xs = (U * torch.clamp(S - lam, min=0.0)) @ Vh
+    e1.record()
+    torch.cuda.synchronize()
+    ms_svd = e0.elapsed_time(e1)
+    return {"workload": "matrix completion 4096x4096, rank 20, Bernoulli(0.2) mask, "
+                        "lambda = 0.02 ||P_Omega(M)||_2, proximal gradient with step 1",
+            "steps": steps, "ms_per_step": ms / steps, "recovery": rec(X),
+            "recovery_at_svd_steps": rec_at,
+            "torch_svd_loop": {"steps": svd_steps, "ms_per_step": ms_svd / svd_steps,
+                               "recovery": rec(Xs)},
+            "speedup_per_step_vs_torch_svd": (ms_svd / svd_steps) / (ms / steps)}
+
+
 def serving_extra(ctx_cls, pkg, torch, dev, n_req=200):
     """Poisson stream through svt_serve_submit / svt_serve_poll: sizes log-uniform
     256-8192 (rounded to powers of two), aspect 1, 2, 1/2, 30 % FP32 tier. Capacity
@@ -361,8 +421,10 @@ def run_ours(args, n):
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     opts = dict(iters=ITERS, prec="bf16", fuse=not args.no_fuse)
+    if args.tile:
+        opts["tile"] = args.tile
 
-    if not args.no_autotune:
+    if not args.no_autotune and not args.tile:
         ctx.autotune(A, TAU, out=Y, reps=2, **opts)  # tile width per product launch
     sampler = ClockSampler(local)
     sampler.start()  # started before the warm-up so its start-up cost is outside the timed region
@@ -500,6 +562,7 @@ def run_ours(args, n):
     if world == 1 and not args.no_extras:
         line["batch"] = batch_extra(pkg.Context, pkg, torch, dev)
         line["serving"] = serving_extra(pkg.Context, pkg, torch, dev)
+        line["completion"] = completion_extra(pkg.Context, pkg, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
         est, desc, cores = oracle_sample(n, 1002, 96, repeats=1)
         line["cpu_baseline"] = {"value": 1.0 / est[0], "unit": "solves/s", "cores": cores,
@@ -522,6 +585,9 @@ def main():
                     help="one launch per product stage instead of the fused persistent launch")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default tile widths instead of svt_autotune")
+    ap.add_argument("--tile", type=int, default=0, choices=[0, 128, 256, 512],
+                    help="product tiles: 0 automatic, 128/256 one CTA per 128 x tile, "
+                         "512 a CTA pair per 256 x 256 tile")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batch and serving measurements")
     ap.add_argument("--only-timed", action="store_true",

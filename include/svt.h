@@ -112,6 +112,14 @@ typedef struct {
                                    rounding until the iteration has spread them);
                                    -1 (default) = every step whose design interval
                                    starts below 0.1 */
+    int tile;                   /* product tiles (BF16 / FP32 tiers, svt_polar_ex):
+                                   0 (default) = automatic (svt_autotune's choice
+                                   when it ran for this shape); 128 or 256 = one
+                                   CTA per 128 x 128 or 128 x 256 tile; 512 = a
+                                   cluster of two CTAs per 256 x 256 tile
+                                   (tcgen05 cta_group::2, each CTA staging half of
+                                   the tile's operands). Batches and serving choose
+                                   their own tiles. Other values: SVT_ERR_INVALID */
 } svt_options;
 
 typedef struct svt_ctx *svt_ctx_t;
@@ -254,6 +262,40 @@ svt_status svt_debug_gemm_bf16(svt_ctx_t ctx, int nseg, const void *L_hi, const 
                                const void *R_hi, const void *R_lo, int64_t M, int64_t N,
                                int64_t K, int64_t ldl, int64_t ldr, float *D, int64_t ldd,
                                int sym, void *stream);
+
+/*
+ * svt_prox_grad_step: one proximal-gradient step of nuclear-norm regularised
+ * matrix completion, the use of singular value soft-thresholding that Section 2
+ * names (SVT is the proximal operator of tau ||.||_*):
+ *   minimise F(X) = 1/2 ||P_Omega(X - M)||_F^2 + lambda ||X||_*,
+ *   Z = X + step P_Omega(M - X);  X <- A_{step lambda}(Z)   (Eq. 1, via svt_polar_ex).
+ * The smooth part's gradient has Lipschitz constant 1, so 0 < step <= 1 does not
+ * increase F.
+ *   X: m x n FP32 device (ldx >= n), the iterate, read and overwritten in place.
+ *   M: m x n FP32 device (ldm >= n), the observed matrix (entries off Omega ignored).
+ *   mask: m x n bytes device (ldw >= n), nonzero = observed (Omega).
+ *   Z: m x n FP32 device scratch (ldz >= n), overlapping none of X, M, mask; holds
+ *      the gradient step on return.
+ *   step: finite, > 0. lambda: finite, >= 0. opt: as svt_polar_ex (NULL = defaults).
+ *   d_status: nullable device word for the solve's device-side status.
+ * Asynchronous on `stream`: a memory-bound masked-update kernel, then the solve.
+ * Errors (before any launch): SVT_ERR_INVALID (null pointers, sizes, leading
+ * dimensions, step, lambda, options, overlapping buffers), SVT_ERR_OOM (the
+ * context's workspace is smaller than svt_workspace_bytes_ex(m, n, opt)),
+ * SVT_ERR_UNSUPPORTED, SVT_ERR_BUSY (serving active), SVT_ERR_CUDA.
+ */
+svt_status svt_prox_grad_step(svt_ctx_t ctx, float *X, int64_t ldx, const float *M, int64_t ldm,
+                              const uint8_t *mask, int64_t ldw, float *Z, int64_t ldz, int64_t m,
+                              int64_t n, float step, float lambda, const svt_options *opt,
+                              svt_status *d_status, void *stream);
+
+/* svt_debug_gemm_bf16 with an explicit tile-width code: 0 = automatic (as
+ * svt_debug_gemm_bf16), 128, 256, or 512 (a cluster of two CTAs per 256 x 256
+ * tile, tcgen05 cta_group::2). Errors: as above; SVT_ERR_INVALID on another tile. */
+svt_status svt_debug_gemm_bf16_ex(svt_ctx_t ctx, int nseg, const void *L_hi, const void *L_lo,
+                                  const void *R_hi, const void *R_lo, int64_t M, int64_t N,
+                                  int64_t K, int64_t ldl, int64_t ldr, float *D, int64_t ldd,
+                                  int sym, int tile, void *stream);
 
 /* Number of kernel launches the library has issued on this context so far
  * (host counter; used to report launches per solve). */

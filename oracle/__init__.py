@@ -15,11 +15,13 @@ Contents (each function cites the passage of the paper it follows):
 * ``svt.svt_polar_plain``: the method step by step as plain FP64 matrix products.
 * ``schedule``: the oracle's own Remez derivation of the odd-polynomial schedules.
 * ``spectral``: exact-arithmetic prediction of the method from the singular values.
+* ``completion``: nuclear-norm matrix completion by proximal gradient with SVT by
+  definition (Section 2's use of SVT), its objective and optimality residuals.
 
 Pins (tests/test_oracle_*.py) tie these to closed forms, invariants, brute force
 and LAPACK. Parity is pinned for every function listed above.
 """
-from . import native, schedule, spectral, svt  # noqa: F401
+from . import completion, native, schedule, spectral, svt  # noqa: F401
 from .native import jacobi_svd  # noqa: F401
 from .svt import (svt_definition, prop1, prop1_footnote, prop1_factored,  # noqa: F401
                   corollary_rank_r, best_rank_r, relerr, gap, svt_polar_plain,

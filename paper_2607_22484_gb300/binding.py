@@ -37,8 +37,10 @@ EXPORTS = [
     "svt_status_str", "svt_options_default", "svt_workspace_bytes_ex", "svt_workspace_bytes",
     "svt_ctx_create", "svt_ctx_destroy", "svt_polar", "svt_polar_ex", "svt_batch",
     "svt_batch_workspace_bytes", "svt_serve_submit", "svt_serve_poll", "svt_serve_release",
-    "svt_ctx_sync", "svt_schedule_coeffs", "svt_debug_gemm_bf16", "svt_ctx_launch_count",
+    "svt_ctx_sync", "svt_schedule_coeffs", "svt_debug_gemm_bf16", "svt_debug_gemm_bf16_ex",
+    "svt_ctx_launch_count",
     "svt_ctx_profile", "svt_ctx_profile_read", "svt_polar_noalloc", "svt_autotune",
+    "svt_prox_grad_step",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -47,7 +49,7 @@ class Options(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("prec", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("norm", ctypes.c_int), ("ell0", ctypes.c_double), ("delta", ctypes.c_double),
                 ("polish", ctypes.c_int), ("mode", ctypes.c_int), ("fuse", ctypes.c_int),
-                ("hp_steps", ctypes.c_int)]
+                ("hp_steps", ctypes.c_int), ("tile", ctypes.c_int)]
 
 
 class Matrix(ctypes.Structure):
@@ -127,7 +129,7 @@ def _check(st: int, where: str):
 
 def make_options(iters: int = 20, prec="bf16", schedule="auto", norm="auto", ell0: float = 1e-3,
                  delta: float = -1.0, polish: bool = True, mode="svt", hp_steps: int = -1,
-                 fuse: bool = True) -> Options:
+                 fuse: bool = True, tile: int = 0) -> Options:
     o = Options()
     lib().svt_options_default(ctypes.byref(o))
     o.iters = int(iters)
@@ -140,6 +142,7 @@ def make_options(iters: int = 20, prec="bf16", schedule="auto", norm="auto", ell
     o.mode = MODE[mode] if isinstance(mode, str) else int(mode)
     o.hp_steps = int(hp_steps)
     o.fuse = 1 if fuse else 0
+    o.tile = int(tile)
     return o
 
 
@@ -252,6 +255,49 @@ class Context:
                "svt_polar_ex")
         return out
 
+    def prox_grad_step(self, X, M, mask, lam: float, Z=None, step: float = 1.0, status=None,
+                       stream=None, **opts):
+        """One proximal-gradient step of nuclear-norm matrix completion through
+        svt_prox_grad_step: Z = X + step P_Omega(M - X); X <- A_{step lam}(Z), in place.
+        mask: CUDA uint8 tensor (nonzero = observed). Returns (X, Z)."""
+        import torch
+        x_ptr, m, n, ldx = _f32_matrix(X, "X")
+        m_ptr, mm, mn, ldm = _f32_matrix(M, "M")
+        if (mm, mn) != (m, n):
+            raise ValueError("M has the wrong shape")
+        if (not isinstance(mask, torch.Tensor) or mask.dtype != torch.uint8 or not mask.is_cuda
+                or tuple(mask.shape) != (m, n) or mask.stride(1) != 1):
+            raise ValueError("mask must be a row-major CUDA uint8 tensor of X's shape")
+        if Z is None:
+            Z = torch.empty((m, n), dtype=torch.float32, device=X.device)
+        z_ptr, zm, zn, ldz = _f32_matrix(Z, "Z")
+        if (zm, zn) != (m, n):
+            raise ValueError("Z has the wrong shape")
+        o = make_options(**opts)
+        self.ensure_workspace(workspace_bytes(m, n, **opts))
+        st_ptr = status.data_ptr() if status is not None else None
+        _check(lib().svt_prox_grad_step(self.handle, ctypes.c_void_p(x_ptr), ldx,
+                                        ctypes.c_void_p(m_ptr), ldm,
+                                        ctypes.c_void_p(mask.data_ptr()), mask.stride(0),
+                                        ctypes.c_void_p(z_ptr), ldz, m, n, ctypes.c_float(step),
+                                        ctypes.c_float(lam), ctypes.byref(o),
+                                        ctypes.c_void_p(st_ptr),
+                                        ctypes.c_void_p(_stream_ptr(stream))),
+               "svt_prox_grad_step")
+        return X, Z
+
+    def complete(self, M, mask, lam: float, steps: int, X=None, step: float = 1.0, status=None,
+                 stream=None, **opts):
+        """`steps` proximal-gradient steps from X (zeros if None); returns X."""
+        import torch
+        if X is None:
+            X = torch.zeros_like(M)
+        Z = torch.empty_like(M)
+        for _ in range(int(steps)):
+            self.prox_grad_step(X, M, mask, lam, Z=Z, step=step, status=status, stream=stream,
+                                **opts)
+        return X
+
     def autotune(self, A, tau: float, out=None, reps: int = 2, stream=None, **opts):
         """Pick the product kernel's tile width per launch for this shape and options
         (svt_autotune); later polar() calls with them use the tuned plan."""
@@ -306,16 +352,16 @@ class Context:
                                ctypes.c_void_p(_stream_ptr(stream))), "svt_polar")
         return out
 
-    def debug_gemm_bf16(self, nseg, L_hi, L_lo, R_hi, R_lo, D, sym=False, stream=None):
-        """D = sum of segment products (see svt_debug_gemm_bf16)."""
+    def debug_gemm_bf16(self, nseg, L_hi, L_lo, R_hi, R_lo, D, sym=False, stream=None, tile=0):
+        """D = sum of segment products (see svt_debug_gemm_bf16_ex)."""
         M, K = L_hi.shape
         N = R_hi.shape[0]
         ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else None)
-        _check(lib().svt_debug_gemm_bf16(self.handle, int(nseg), ptr(L_hi), ptr(L_lo), ptr(R_hi),
-                                         ptr(R_lo), M, N, K, L_hi.stride(0), R_hi.stride(0),
-                                         ptr(D), D.stride(0), 1 if sym else 0,
-                                         ctypes.c_void_p(_stream_ptr(stream))),
-               "svt_debug_gemm_bf16")
+        _check(lib().svt_debug_gemm_bf16_ex(self.handle, int(nseg), ptr(L_hi), ptr(L_lo),
+                                            ptr(R_hi), ptr(R_lo), M, N, K, L_hi.stride(0),
+                                            R_hi.stride(0), ptr(D), D.stride(0), 1 if sym else 0,
+                                            int(tile), ctypes.c_void_p(_stream_ptr(stream))),
+               "svt_debug_gemm_bf16_ex")
         return D
 
     def _matrix(self, A, tau, out, status, opts):

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libsvt.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gemm_tc.cu", "aux_kernels.cu", "svt_api.cu", "serve.cpp", "schedule.cpp", "noalloc.cu"]
+SOURCES = ["gemm_tc.cu", "aux_kernels.cu", "svt_api.cu", "serve.cpp", "schedule.cpp", "noalloc.cu",
+           "completion.cu"]
 
 
 def _nvcc() -> str:

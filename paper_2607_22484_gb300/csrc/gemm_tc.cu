@@ -16,10 +16,20 @@
 // Two accumulator buffers of BN FP32 columns each let the epilogue of one tile
 // overlap the MMAs of the next.
 //
+// CTA-pair mode (PAIR): a cluster of two CTAs computes one 256 x 256 tile with
+// tcgen05.mma.cta_group::2. Each CTA stages its own 128 rows of L and one half
+// (128 rows) of the tile's R, so a pipeline stage is 32 KiB instead of 48 KiB
+// and every operand byte crosses L2 -> SM once per pair instead of once per CTA.
+// The even CTA (leader) issues the MMAs for both, its barriers collect both
+// CTAs' TMA bytes and both CTAs' epilogue releases; MMA completion is multicast
+// to both CTAs, whose epilogues each drain their own 128 x 256 accumulator.
+//
 // Every wait on an mbarrier is bounded (kWaitTimeoutNs of global time); on
 // expiry the kernel records SVT_ERR_TIMEOUT in the problem's status word, the
 // other roles stop at their next wait, in-flight copies and MMAs are drained
 // (again with a bound) and tensor memory is released before the kernel returns.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -99,6 +109,96 @@ __device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_fl
             }
         }
     }
+}
+
+// Waits on barriers that another CTA of the cluster signals use acquire at
+// cluster scope.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                  int *status, uint64_t limit_ns)
+{
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait_cluster(bar, parity))
+            return true;
+        if ((it & 255u) == 255u) {
+            if (*abort_flag)
+                return false;
+            uint64_t now = global_timer_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > limit_ns) {
+                *abort_flag = 1;
+                if (status)
+                    atomicCAS(status, 0, (int)SVT_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+template <bool CLUSTER>
+__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                         int *status, uint64_t limit_ns)
+{
+    return CLUSTER ? mbar_wait_cluster(bar, parity, abort_flag, status, limit_ns)
+                   : mbar_wait(bar, parity, abort_flag, status, limit_ns);
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t peer_addr(const void *p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_remote_u32(uint32_t cluster_addr, int v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// TMA load into this CTA's shared memory whose completion is counted on a
+// barrier of either CTA of the pair (a shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(void *smem_dst, const CUtensorMap *map, int x,
+                                                 int y, uint32_t bar_cluster_addr)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cluster_addr)
+        : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *map, int x, int y,
@@ -196,6 +296,66 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
         : "memory");
 }
 
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t a, uint64_t b,
+                                              uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// Completion of this thread's pair MMAs arrives on the barrier at the same
+// offset in both CTAs of the pair.
+__device__ __forceinline__ void mma_commit_both(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(smem_u32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_pair_local(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t cols)
+{
+    if (PAIR)
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(slot)),
+                     "r"(cols));
+    else
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(slot)),
+                     "r"(cols));
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void tmem_relinquish()
+{
+    if (PAIR)
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    else
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void tmem_dealloc(uint32_t base, uint32_t cols)
+{
+    if (PAIR)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(cols));
+    else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(cols));
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -232,11 +392,11 @@ __device__ __forceinline__ const TcProblem &prob_at(const TcLaunch &L, int p)
     return L.gtab ? L.gtab[p] : L.p[p];
 }
 
-// Linear tile index -> (problem, tile row, tile column).
+// Linear tile index -> (problem, tile row, tile column) for tiles of TM x BN.
 // Dense problems: column-major over the tile grid. Symmetric problems: only
 // tiles holding some element with row <= col; column tn holds r (tn + 1) row
-// tiles (r = BN / BM), so the first tile of column tn is r tn (tn + 1) / 2.
-template <int BN>
+// tiles (r = BN / TM), so the first tile of column tn is r tn (tn + 1) / 2.
+template <int BN, int TM>
 __device__ TileCoord decode_tile(const TcLaunch &L, int t)
 {
     TileCoord tc{0, 0, 0, false};
@@ -266,7 +426,7 @@ __device__ TileCoord decode_tile(const TcLaunch &L, int t)
         tc.valid = true;
         return tc;
     }
-    constexpr int r = BN / kBM;
+    constexpr int r = BN / TM;
     int tn = (int)((sqrtf(8.0f * (float)local / (float)r + 1.0f) - 1.0f) * 0.5f);
     while (tn > 0 && r * tn * (tn + 1) / 2 > local)
         --tn;
@@ -637,14 +797,17 @@ __device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiOver
 
 constexpr int kRingTiles = 4;  // fused launches: tile ids in flight between the roles
 
-template <int BN, int STAGES, bool CHAIN>
+template <int BN, int STAGES, bool CHAIN, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcLaunch L)
 {
+    static_assert(!PAIR || BN == 256, "CTA pairs compute 256 x 256 tiles");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                 ~static_cast<uintptr_t>(1023));
     constexpr int A_BYTES = kBM * kBK * 2;
-    constexpr int B_BYTES = BN * kBK * 2;
+    constexpr int B_ROWS = PAIR ? BN / 2 : BN;  // rows of R this CTA stages per k-block
+    constexpr int B_BYTES = B_ROWS * kBK * 2;
+    constexpr int TILE_ROWS = PAIR ? 2 * kBM : kBM;
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * A_BYTES;
     uint8_t *stage_all = sB + STAGES * B_BYTES;  // kEpiWarps x 4 KiB, 1024-aligned
@@ -666,6 +829,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     int *status0 = prob_at(L, 0).ep.status;
+    // CTA pairs: rank 0 (leader) issues the MMAs and hands out tile ids.
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    const bool leader = rank == 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -674,29 +840,38 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 32 * kEpiWarps);
+            // Pairs: one release per epilogue warp of both CTAs, on the leader's barrier.
+            mbar_init(&tempty[b], PAIR ? 2 * kEpiWarps : 32 * kEpiWarps);
         }
         mbar_init(drain, 1);
         for (int i = 0; i < kRingTiles; ++i) {
             mbar_init(&rfull[i], 1);
-            mbar_init(&rempty[i], 1 + kEpiWarps);
+            // Consumers of a ring entry: the MMA issuer and the epilogue warps; for
+            // pairs also the peer's producer and epilogue warps.
+            mbar_init(&rempty[i], PAIR ? 2 * (1 + kEpiWarps) : 1 + kEpiWarps);
         }
         *abort_flag = 0;
         // A solve whose earlier launch already timed out does no further work.
         *skip_flag = (status0 && *reinterpret_cast<volatile int *>(status0) == (int)SVT_ERR_TIMEOUT);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (PAIR) {
+        // The peer's barriers exist before either CTA signals them.
+        __syncthreads();
+        cluster_sync_all();
+    }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tmem_slot)),
-                     "r"(2 * BN));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        tmem_alloc<PAIR>(tmem_slot, 2 * BN);
+        tmem_relinquish<PAIR>();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     const int total = *skip_flag ? 0 : (L.gtab ? L.gstart[L.gcount] : L.tile_start[L.nprob]);
+    // Static schedule (non-fused launches): CTA (pair) i takes tiles i, i + grid, ...
+    const int t_first = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int t_step = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------ TMA producer
@@ -706,26 +881,43 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         bool ok = true;
         int ri = 0;
         uint32_t rphase = 0;
-        for (int it = 0, t = blockIdx.x; ok; ++it, t += gridDim.x) {
+        for (int t = t_first; ok; t += t_step) {
             if (CHAIN) {
-                // Take the next tile in table order and hand its id to the other roles.
-                if (!mbar_wait(&rempty[ri], rphase ^ 1u, abort_flag, status0, kWaitTimeoutNs))
-                    break;
-                t = atomicAdd(L.tile_counter, 1);
-                tring[ri] = (t < total) ? t : -1;
-                mbar_arrive(&rfull[ri]);
+                if (!PAIR || leader) {
+                    // Take the next tile in table order and hand its id to the other roles.
+                    if (!wait_bar<PAIR>(&rempty[ri], rphase ^ 1u, abort_flag, status0, kWaitTimeoutNs))
+                        break;
+                    t = atomicAdd(L.tile_counter, 1);
+                    t = (t < total) ? t : -1;
+                    tring[ri] = t;
+                    if (PAIR) {
+                        st_remote_u32(peer_addr((const void *)&tring[ri], 1), t);
+                        mbar_arrive_remote(peer_addr(&rfull[ri], 1));
+                    }
+                    mbar_arrive(&rfull[ri]);
+                } else {
+                    // Peer CTA: the leader's tile id.
+                    if (!mbar_wait_cluster(&rfull[ri], rphase, abort_flag, status0, kWaitTimeoutNs))
+                        break;
+                    t = tring[ri];
+                    mbar_arrive_remote(peer_addr(&rempty[ri], 0));
+                }
                 if (++ri == kRingTiles) {
                     ri = 0;
                     rphase ^= 1u;
                 }
-            }
-            if (t >= total)
+                if (t < 0)
+                    break;
+            } else if (t >= total) {
                 break;
-            TileCoord tc = decode_tile<BN>(L, t);
+            }
+            TileCoord tc = decode_tile<BN, TILE_ROWS>(L, t);
             if (!tc.valid)
                 continue;
             const TcProblem &P = prob_at(L, tc.prob);
             const int kblocks = (P.K + kBK - 1) / kBK;
+            const int row0 = (PAIR ? 2 * tc.tm + (int)rank : tc.tm) * kBM;
+            const int col0 = tc.tn * BN + (int)rank * B_ROWS;
             if (CHAIN) {
                 // Operands are results of earlier problems: wait until they are complete.
                 for (int d = 0; d < 2 && ok; ++d)
@@ -740,13 +932,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 const CUtensorMap *mL = &P.mapL[P.segL[sg]];
                 const CUtensorMap *mR = &P.mapR[P.segR[sg]];
                 for (int kb = 0; kb < kblocks; ++kb) {
-                    if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, status0, kWaitTimeoutNs)) {
+                    if (!wait_bar<PAIR>(&empty[stage], phase ^ 1u, abort_flag, status0, kWaitTimeoutNs)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&full[stage], (uint32_t)(A_BYTES + B_BYTES));
-                    tma_load_2d(sA + stage * A_BYTES, mL, kb * kBK, tc.tm * kBM, &full[stage]);
-                    tma_load_2d(sB + stage * B_BYTES, mR, kb * kBK, tc.tn * BN, &full[stage]);
+                    if (PAIR) {
+                        // Both CTAs' bytes complete on the leader's barrier.
+                        const uint32_t fb = peer_addr(&full[stage], 0);
+                        if (leader)
+                            mbar_expect_tx(&full[stage], 2u * (uint32_t)(A_BYTES + B_BYTES));
+                        tma_load_2d_pair(sA + stage * A_BYTES, mL, kb * kBK, row0, fb);
+                        tma_load_2d_pair(sB + stage * B_BYTES, mR, kb * kBK, col0, fb);
+                    } else {
+                        mbar_expect_tx(&full[stage], (uint32_t)(A_BYTES + B_BYTES));
+                        tma_load_2d(sA + stage * A_BYTES, mL, kb * kBK, row0, &full[stage]);
+                        tma_load_2d(sB + stage * B_BYTES, mR, kb * kBK, col0, &full[stage]);
+                    }
                     issued |= 1u << stage;
                     issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
                     if (++stage == STAGES) {
@@ -756,15 +957,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 }
             }
         }
-        // Drain: the last copy into every stage must have landed before exit.
+        // Drain: the last copy into every stage must have landed before exit. The
+        // peer of a pair sees its copies land through the leader's MMA consuming them.
         for (int s = 0; s < STAGES; ++s)
             if ((issued >> s) & 1u) {
                 volatile int no_abort = 0;
-                mbar_wait(&full[s], (issued_parity >> s) & 1u, &no_abort, nullptr, kWaitTimeoutNs / 4);
+                if (!PAIR || leader)
+                    mbar_wait(&full[s], (issued_parity >> s) & 1u, &no_abort, nullptr, kWaitTimeoutNs / 4);
+                else
+                    mbar_wait_cluster(&empty[s], (issued_parity >> s) & 1u, &no_abort, nullptr,
+                                      kWaitTimeoutNs / 4);
             }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 1 && lane == 0 && (!PAIR || leader)) {
         // ------------------------------------------------ MMA issuer
-        constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+        constexpr uint32_t idesc = idesc_bf16(TILE_ROWS, BN);
         int stage = 0;
         uint32_t phase = 0;
         int buf = 0;
@@ -772,7 +978,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         bool ok = true;
         int ri = 0;
         uint32_t rphase = 0;
-        for (int t = blockIdx.x; ok; t += gridDim.x) {
+        for (int t = t_first; ok; t += t_step) {
             if (CHAIN) {
                 if (!mbar_wait(&rfull[ri], rphase, abort_flag, status0, kWaitTimeoutNs))
                     break;
@@ -787,12 +993,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             } else if (t >= total) {
                 break;
             }
-            TileCoord tc = decode_tile<BN>(L, t);
+            TileCoord tc = decode_tile<BN, TILE_ROWS>(L, t);
             if (!tc.valid)
                 continue;
             const TcProblem &P = prob_at(L, tc.prob);
             const int kblocks = (P.K + kBK - 1) / kBK;
-            if (!mbar_wait(&tempty[buf], tphase ^ 1u, abort_flag, status0, kWaitTimeoutNs))
+            if (!wait_bar<PAIR>(&tempty[buf], tphase ^ 1u, abort_flag, status0, kWaitTimeoutNs))
                 break;
             tc_fence_after();
             const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
@@ -808,11 +1014,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                     const uint32_t b0 = smem_u32(sB + stage * B_BYTES);
 #pragma unroll
                     for (int kk = 0; kk < kBK / 16; ++kk) {
-                        mma_bf16(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
-                                 acc);
+                        if (PAIR)
+                            mma_bf16_pair(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32),
+                                          idesc, acc);
+                        else
+                            mma_bf16(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32),
+                                     idesc, acc);
                         acc = 1;
                     }
-                    mma_commit(&empty[stage]);
+                    if (PAIR)
+                        mma_commit_both(&empty[stage]);
+                    else
+                        mma_commit(&empty[stage]);
                     if (++stage == STAGES) {
                         stage = 0;
                         phase ^= 1u;
@@ -821,14 +1034,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             }
             if (!ok)
                 break;
-            mma_commit(&tfull[buf]);
+            if (PAIR)
+                mma_commit_both(&tfull[buf]);
+            else
+                mma_commit(&tfull[buf]);
             if (++buf == 2) {
                 buf = 0;
                 tphase ^= 1u;
             }
         }
         // Drain: every MMA issued so far completes before tensor memory is freed.
-        mma_commit(drain);
+        if (PAIR)
+            mma_commit_pair_local(drain);
+        else
+            mma_commit(drain);
         volatile int no_abort = 0;
         mbar_wait(drain, 0, &no_abort, nullptr, kWaitTimeoutNs / 4);
     } else if (warp >= 2) {
@@ -843,14 +1062,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         EpiOverride ov{nullptr, 0, nullptr, 0, 0};
         int ri = 0;
         uint32_t rphase = 0;
-        for (int t = blockIdx.x;; t += gridDim.x) {
+        for (int t = t_first;; t += t_step) {
             if (CHAIN) {
-                if (!mbar_wait(&rfull[ri], rphase, abort_flag, status0, kWaitTimeoutNs))
+                if (!wait_bar<PAIR>(&rfull[ri], rphase, abort_flag, status0, kWaitTimeoutNs))
                     break;
                 t = tring[ri];
                 __syncwarp();
-                if (lane == 0)
-                    mbar_arrive(&rempty[ri]);
+                if (lane == 0) {
+                    if (PAIR && !leader)
+                        mbar_arrive_remote(peer_addr(&rempty[ri], 0));
+                    else
+                        mbar_arrive(&rempty[ri]);
+                }
                 if (++ri == kRingTiles) {
                     ri = 0;
                     rphase ^= 1u;
@@ -860,9 +1083,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             } else if (t >= total) {
                 break;
             }
-            TileCoord tc = decode_tile<BN>(L, t);
+            TileCoord tc = decode_tile<BN, TILE_ROWS>(L, t);
             if (!tc.valid)
                 continue;
+            if (PAIR)
+                tc.tm = 2 * tc.tm + (int)rank;  // this CTA's 128-row half of the tile
             const TcProblem &P = prob_at(L, tc.prob);
             if (CHAIN && (P.ep.c_kind != C_NONE || P.ep.theta_src)) {
                 // C or the norm bound is an earlier result: make it visible to these loads.
@@ -896,7 +1121,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 sc = epi_scales(P.ep, alpha);
                 last_prob = tc.prob;
             }
-            if (!mbar_wait(&tfull[buf], tphase, abort_flag, status0, kWaitTimeoutNs))
+            if (!wait_bar<PAIR>(&tfull[buf], tphase, abort_flag, status0, kWaitTimeoutNs))
                 break;
             tc_fence_after();
             const int64_t warp_row0 = (int64_t)tc.tm * kBM + quad * 32;
@@ -921,7 +1146,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                     atomicAdd(P.ep.norm_acc, nrm);
             }
             tc_fence_before();
-            mbar_arrive(&tempty[buf]);
+            if (PAIR) {
+                // One release per warp, on the leader's barrier (it issues the next MMAs).
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive_remote(peer_addr(&tempty[buf], 0));
+            } else {
+                mbar_arrive(&tempty[buf]);
+            }
             if (++buf == 2) {
                 buf = 0;
                 tphase ^= 1u;
@@ -947,56 +1179,77 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 
     tc_fence_before();
     __syncthreads();
+    if (PAIR)
+        cluster_sync_all();  // neither CTA leaves while its peer may still signal it
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                     "r"(2 * BN));
+        tmem_dealloc<PAIR>(tmem_base, 2 * BN);
     }
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool PAIR>
 constexpr int smem_bytes()
 {
-    return STAGES * (kBM + BN) * kBK * 2 + kEpiWarps * 4096 /* epilogue staging */ +
-           1024 /* alignment slack */ + 512 /* barriers, tile ring */;
+    return STAGES * (kBM + (PAIR ? BN / 2 : BN)) * kBK * 2 +
+           kEpiWarps * 4096 /* epilogue staging */ + 1024 /* alignment slack */ +
+           512 /* barriers, tile ring */;
 }
 
-template <int BN, int STAGES>
-cudaError_t launch_bn(const TcLaunch &l, int num_sms, cudaStream_t s)
+// One launch of the product kernel over total_tiles tiles (tile-width code's
+// tiles: CTA pairs for kBnPair). Persistent: at most one CTA (pair) per SM (pair).
+template <int BN, int STAGES, bool CHAIN, bool PAIR>
+cudaError_t launch_kernel(const TcLaunch &l, int total_tiles, int num_sms, cudaStream_t s)
 {
-    static bool configured = false;
-    constexpr int smem = smem_bytes<BN, STAGES>();
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess)
-            return e;
-        configured = true;
-    }
-    int total = l.gtab ? -1 : l.tile_start[l.nprob];
-    if (total == 0)
-        return cudaSuccess;
-    if (total < 0)
-        total = num_sms;  // grouped launch: the tile count lives on the device
-    int grid = total < num_sms ? total : num_sms;
-    tc_gemm_kernel<BN, STAGES, false><<<grid, kThreads, smem, s>>>(l);
-    return cudaGetLastError();
-}
-
-template <int BN, int STAGES, bool CHAIN>
-cudaError_t launch_table(const TcLaunch &l, int total_tiles, int num_sms, cudaStream_t s)
-{
-    constexpr int smem = smem_bytes<BN, STAGES>();
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, CHAIN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    constexpr int smem = smem_bytes<BN, STAGES, PAIR>();
+    static_assert(smem <= 232448, "shared memory per CTA");
+    auto kern = tc_gemm_kernel<BN, STAGES, CHAIN, PAIR>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess)
         return e;
     if (total_tiles <= 0)
         return cudaSuccess;
-    const int grid = total_tiles < num_sms ? total_tiles : num_sms;
-    tc_gemm_kernel<BN, STAGES, CHAIN><<<grid, kThreads, smem, s>>>(l);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    int grid = total_tiles < num_sms ? total_tiles : num_sms;
+    if (PAIR) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        // Pairs that can be resident at once (SMs pair up within a GPC).
+        static int max_pairs = -1;
+        if (max_pairs < 0) {
+            cfg.gridDim = dim3((unsigned)(num_sms & ~1), 1, 1);
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess || nc <= 0) {
+                cudaGetLastError();
+                nc = num_sms / 2;
+            }
+            max_pairs = nc;
+        }
+        const int pairs = total_tiles < max_pairs ? total_tiles : max_pairs;
+        grid = 2 * pairs;
+    }
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    return cudaLaunchKernelEx(&cfg, kern, l);
+}
+
+template <bool CHAIN>
+cudaError_t launch_width(const TcLaunch &l, int bn, int total_tiles, int num_sms, cudaStream_t s)
+{
+    if (bn == 256)
+        return launch_kernel<256, 4, CHAIN, false>(l, total_tiles, num_sms, s);
+    if (bn == 128)
+        return launch_kernel<128, 6, CHAIN, false>(l, total_tiles, num_sms, s);
+    if (bn == kBnPair)
+        return launch_kernel<256, 6, CHAIN, true>(l, total_tiles, num_sms, s);
+    return cudaErrorInvalidValue;
 }
 
 } // namespace
@@ -1006,11 +1259,7 @@ cudaError_t tc_gemm_launch_grouped(const TcLaunch &l, int bn, int total_tiles, i
 {
     TcLaunch g = l;
     g.nprob = 0;
-    if (bn == 256)
-        return launch_table<256, 4, false>(g, total_tiles, num_sms, s);
-    if (bn == 128)
-        return launch_table<128, 6, false>(g, total_tiles, num_sms, s);
-    return cudaErrorInvalidValue;
+    return launch_width<false>(g, bn, total_tiles, num_sms, s);
 }
 
 cudaError_t tc_gemm_launch_fused(const TcLaunch &l, int bn, int total_tiles, int num_sms,
@@ -1018,28 +1267,35 @@ cudaError_t tc_gemm_launch_fused(const TcLaunch &l, int bn, int total_tiles, int
 {
     TcLaunch g = l;
     g.nprob = 0;
-    if (bn == 256)
-        return launch_table<256, 4, true>(g, total_tiles, num_sms, s);
-    if (bn == 128)
-        return launch_table<128, 6, true>(g, total_tiles, num_sms, s);
-    return cudaErrorInvalidValue;
+    return launch_width<true>(g, bn, total_tiles, num_sms, s);
 }
 
 int tc_num_tiles(const TcProblem &p, int bn)
 {
     if (!p.sym)
         return p.tiles_m * p.tiles_n;
-    int r = bn / kBM;
+    const int r = tile_cols(bn) / tile_rows(bn);
     return r * p.tiles_n * (p.tiles_n + 1) / 2;
+}
+
+int tc_valid_ctas(const TcProblem &p, int bn)
+{
+    int n = 0;
+    if (!p.sym) {
+        n = p.tiles_m * p.tiles_n;
+    } else {
+        const int r = tile_cols(bn) / tile_rows(bn);
+        for (int tn = 0; tn < p.tiles_n; ++tn)
+            n += std::min(r * (tn + 1), p.tiles_m);
+    }
+    return n * ctas_per_tile(bn);
 }
 
 cudaError_t tc_gemm_launch(const TcLaunch &l, int bn, int num_sms, cudaStream_t s)
 {
-    if (bn == 256)
-        return launch_bn<256, 4>(l, num_sms, s);
-    if (bn == 128)
-        return launch_bn<128, 6>(l, num_sms, s);
-    return cudaErrorInvalidValue;
+    if (l.gtab)
+        return cudaErrorInvalidValue;
+    return launch_width<false>(l, bn, l.tile_start[l.nprob], num_sms, s);
 }
 
 } // namespace svt

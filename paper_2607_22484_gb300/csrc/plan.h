@@ -35,6 +35,7 @@ struct Resolved {
     int mode;
     int hp_steps;   // leading S-chain steps in the FP32-class tier (BF16 tier)
     int fuse;       // one persistent launch for all products of a solve
+    int tile;       // requested tile-width code (0 automatic); read by svt_polar_ex only
 };
 
 bool resolve(const svt_options *in, Resolved *r);

@@ -175,17 +175,6 @@ size_t batch_table_bytes(int count, const Resolved &r)
            align_up(sizeof(TcProblem) * nprob, kAlign) + 2 * align_up(sizeof(int) * (nprob + 1), kAlign);
 }
 
-int batch_valid_tiles(const TcProblem &p, int bn)
-{
-    if (!p.sym)
-        return p.tiles_m * p.tiles_n;
-    const int r = bn / kBM;
-    int n = 0;
-    for (int tn = 0; tn < p.tiles_n; ++tn)
-        n += std::min(r * (tn + 1), p.tiles_m);
-    return n;
-}
-
 bool same_options(const Resolved &a, const Resolved &b)
 {
     return a.iters == b.iters && a.prec == b.prec && a.schedule == b.schedule && a.norm == b.norm &&
@@ -724,7 +713,7 @@ svt_status build_batch(svt_ctx *ctx, ServeState *s, const svt_matrix *mats, int 
                         tp.dep_target[d] = kEpiWarpsPublic * valid[tp.dep[d]];
                 starts.push_back(total);
                 total += tc_num_tiles(tp, bn);
-                valid.push_back(batch_valid_tiles(tp, bn));
+                valid.push_back(tc_valid_ctas(tp, bn));
                 if (chain < 2)
                     lastp[i][chain] = tp.pid;
                 else

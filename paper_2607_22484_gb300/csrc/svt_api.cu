@@ -153,6 +153,9 @@ bool resolve(const svt_options *in, Resolved *r)
         return false;
     r->hp_steps = (o.prec == SVT_BF16) ? o.hp_steps : 0;
     r->fuse = (o.fuse && o.prec != SVT_FP64) ? 1 : 0;
+    if (o.tile != 0 && o.tile != 128 && o.tile != 256 && o.tile != kBnPair)
+        return false;
+    r->tile = (o.prec == SVT_FP64) ? 0 : o.tile;
     return true;
 }
 
@@ -294,11 +297,11 @@ struct Builder {
         std::memset(&p, 0, sizeof(p));
         if (!encode_bf16_map(&p.mapL[0], ptr(L.hi), L.rows, L.cols, L.ld, kBM))
             return false;
-        if (!encode_bf16_map(&p.mapR[0], ptr(R.hi), R.rows, R.cols, R.ld, bn))
+        if (!encode_bf16_map(&p.mapR[0], ptr(R.hi), R.rows, R.cols, R.ld, r_box_rows(bn)))
             return false;
         if (L.has_lo && !encode_bf16_map(&p.mapL[1], ptr(L.lo), L.rows, L.cols, L.ld, kBM))
             return false;
-        if (R.has_lo && !encode_bf16_map(&p.mapR[1], ptr(R.lo), R.rows, R.cols, R.ld, bn))
+        if (R.has_lo && !encode_bf16_map(&p.mapR[1], ptr(R.lo), R.rows, R.cols, R.ld, r_box_rows(bn)))
             return false;
         int ns = 0;
         p.segL[ns] = 0; p.segR[ns] = 0; ++ns;
@@ -309,8 +312,8 @@ struct Builder {
         p.N = N;
         p.K = K;
         p.sym = sym ? 1 : 0;
-        p.tiles_m = (M + kBM - 1) / kBM;
-        p.tiles_n = (N + bn - 1) / bn;
+        p.tiles_m = (M + tile_rows(bn) - 1) / tile_rows(bn);
+        p.tiles_n = (N + tile_cols(bn) - 1) / tile_cols(bn);
         p.ep = e;
         attach_store_maps(p);
         return true;
@@ -853,17 +856,6 @@ svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s)
 
 namespace {
 
-int valid_tiles(const TcProblem &p, int bn)
-{
-    if (!p.sym)
-        return p.tiles_m * p.tiles_n;
-    const int r = bn / kBM;
-    int n = 0;
-    for (int tn = 0; tn < p.tiles_n; ++tn)
-        n += std::min(r * (tn + 1), p.tiles_m);
-    return n;
-}
-
 // One persistent launch for all products of the plan: problems in program order,
 // each depending on the previous problem of its chain (the combine on both chains).
 // Eligible when the products are contiguous in the op list and share one tile width.
@@ -920,7 +912,7 @@ svt_status build_fused(svt_ctx *ctx, Plan &P)
                     tp.dep_target[d] = kEpiWarpsPublic * valid[tp.dep[d]];
             starts.push_back(total);
             total += tc_num_tiles(tp, bn);
-            valid.push_back(valid_tiles(tp, bn));
+            valid.push_back(tc_valid_ctas(tp, bn));
             if (chain < 2)
                 lastp[chain] = tp.pid;
             else
@@ -1081,6 +1073,7 @@ void svt_options_default(svt_options *o)
     o->mode = SVT_MODE_SVT;
     o->hp_steps = -1;
     o->fuse = 1;
+    o->tile = 0;
 }
 
 svt_status svt_workspace_bytes_ex(int64_t m, int64_t n, const svt_options *opt, size_t *out)
@@ -1164,7 +1157,7 @@ svt_status svt_polar_ex(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int
     if (cudaSetDevice(ctx->device) != cudaSuccess)
         return SVT_ERR_CUDA;
     Plan *plan = nullptr;
-    const int fbn = ctx->tuning.count(tune_key(m, n, r)) ? -1 : 0;
+    const int fbn = r.tile ? r.tile : (ctx->tuning.count(tune_key(m, n, r)) ? -1 : 0);
     st = get_plan(ctx, m, n, r, 0, ctx->ws_bytes, &plan, fbn);
     if (st != SVT_OK)
         return st;
@@ -1296,27 +1289,29 @@ svt_status svt_ctx_profile_read(svt_ctx_t ctx, double *tc_ms, double *tc_flops,
     return SVT_OK;
 }
 
-svt_status svt_debug_gemm_bf16(svt_ctx_t ctx, int nseg, const void *L_hi, const void *L_lo,
-                               const void *R_hi, const void *R_lo, int64_t M, int64_t N,
-                               int64_t K, int64_t ldl, int64_t ldr, float *D, int64_t ldd,
-                               int sym, void *stream)
+svt_status svt_debug_gemm_bf16_ex(svt_ctx_t ctx, int nseg, const void *L_hi, const void *L_lo,
+                                  const void *R_hi, const void *R_lo, int64_t M, int64_t N,
+                                  int64_t K, int64_t ldl, int64_t ldr, float *D, int64_t ldd,
+                                  int sym, int tile, void *stream)
 {
     if (!ctx || nseg < 1 || nseg > 3 || !L_hi || !R_hi || !D || M <= 0 || N <= 0 || K <= 0 ||
         ldl < K || ldr < K || ldd < N || (ldl % 8) || (ldr % 8) || (sym && M != N))
         return SVT_ERR_INVALID;
     if ((nseg >= 2 && !R_lo) || (nseg == 3 && !L_lo))
         return SVT_ERR_INVALID;
+    if (tile != 0 && tile != 128 && tile != 256 && tile != kBnPair)
+        return SVT_ERR_INVALID;
     if (M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2)
         return SVT_ERR_UNSUPPORTED;
-    const int bn = N > 128 ? 256 : 128;
+    const int bn = tile ? tile : (N > 128 ? 256 : 128);
     TcLaunch l;
     std::memset(&l, 0, sizeof(l));
     l.nprob = 1;
     TcProblem &p = l.p[0];
     if (!encode_bf16_map(&p.mapL[0], L_hi, M, K, ldl, kBM) ||
-        !encode_bf16_map(&p.mapR[0], R_hi, N, K, ldr, bn))
+        !encode_bf16_map(&p.mapR[0], R_hi, N, K, ldr, r_box_rows(bn)))
         return SVT_ERR_INVALID;
-    if (nseg >= 2 && !encode_bf16_map(&p.mapR[1], R_lo, N, K, ldr, bn))
+    if (nseg >= 2 && !encode_bf16_map(&p.mapR[1], R_lo, N, K, ldr, r_box_rows(bn)))
         return SVT_ERR_INVALID;
     if (nseg == 3 && !encode_bf16_map(&p.mapL[1], L_lo, M, K, ldl, kBM))
         return SVT_ERR_INVALID;
@@ -1330,8 +1325,8 @@ svt_status svt_debug_gemm_bf16(svt_ctx_t ctx, int nseg, const void *L_hi, const 
     p.N = (int)N;
     p.K = (int)K;
     p.sym = sym ? 1 : 0;
-    p.tiles_m = (int)((M + kBM - 1) / kBM);
-    p.tiles_n = (int)((N + bn - 1) / bn);
+    p.tiles_m = (int)((M + tile_rows(bn) - 1) / tile_rows(bn));
+    p.tiles_n = (int)((N + tile_cols(bn) - 1) / tile_cols(bn));
     std::memset(&p.ep, 0, sizeof(p.ep));
     p.ep.alpha = 1.0;
     p.ep.o_kind = O_F32;
@@ -1345,6 +1340,15 @@ svt_status svt_debug_gemm_bf16(svt_ctx_t ctx, int nseg, const void *L_hi, const 
     cudaError_t e = tc_gemm_launch(l, bn, ctx->num_sms, static_cast<cudaStream_t>(stream));
     ctx->launches += 1;
     return e == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;
+}
+
+svt_status svt_debug_gemm_bf16(svt_ctx_t ctx, int nseg, const void *L_hi, const void *L_lo,
+                               const void *R_hi, const void *R_lo, int64_t M, int64_t N,
+                               int64_t K, int64_t ldl, int64_t ldr, float *D, int64_t ldd,
+                               int sym, void *stream)
+{
+    return svt_debug_gemm_bf16_ex(ctx, nseg, L_hi, L_lo, R_hi, R_lo, M, N, K, ldl, ldr, D, ldd,
+                                  sym, 0, stream);
 }
 
 } // extern "C"

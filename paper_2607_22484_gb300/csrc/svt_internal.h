@@ -24,6 +24,16 @@ constexpr int kMaxProblems = 2;   // problems per by-value grouped launch (P and
 constexpr int kBM = 128;          // tile rows (tcgen05 M)
 constexpr int kBK = 64;           // K per pipeline stage: one 128-byte swizzle row of BF16
 
+// Tile-width codes of the product kernel. 128 and 256: one CTA per 128 x bn
+// output tile. kBnPair: a cluster of two CTAs per 256 x 256 tile
+// (tcgen05 cta_group::2), each CTA holding 128 x 256 of it and staging half of
+// the tile's R rows.
+constexpr int kBnPair = 512;
+inline int tile_rows(int bn) { return bn == kBnPair ? 2 * kBM : kBM; }
+inline int tile_cols(int bn) { return bn == kBnPair ? 256 : bn; }
+inline int r_box_rows(int bn) { return bn == kBnPair ? 128 : bn; }  // R rows one CTA loads
+inline int ctas_per_tile(int bn) { return bn == kBnPair ? 2 : 1; }
+
 enum CKind : int { C_NONE = 0, C_BF16 = 1, C_PAIR = 2, C_F32 = 3, C_F64 = 4 };
 enum OKind : int { O_NONE = 0, O_BF16 = 1, O_PAIR = 2, O_F32 = 3, O_F64 = 4 };
 
@@ -129,6 +139,9 @@ struct F64Launch {
 
 // ---- launchers (defined in the .cu files) ----
 int tc_num_tiles(const TcProblem &p, int bn);
+// CTA tiles (128 rows each) of a problem that publish completion in a fused
+// launch: tiles with work, times the CTAs per tile.
+int tc_valid_ctas(const TcProblem &p, int bn);
 cudaError_t tc_gemm_launch(const TcLaunch &l, int bn, int num_sms, cudaStream_t s);
 // Grouped launch: l.gtab / l.gstart / l.gcount / l.calls point to device memory;
 // total_tiles (host copy of gstart[gcount]) sizes the grid.

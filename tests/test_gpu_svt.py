@@ -183,3 +183,28 @@ def test_fused_launch_matches_separate_launches(ctx, prec, shape):
     assert oracle.relerr(y1.cpu().numpy(), y0.cpu().numpy()) < 1e-5
     exact = oracle.svt_definition(a.astype(np.float64), 0.3)
     assert oracle.relerr(y1.cpu().numpy(), exact) < TOL[prec]
+
+
+@pytest.mark.parametrize("fuse", [True, False])
+@pytest.mark.parametrize("prec,shape", [("bf16", (520, 384)), ("fp32", (300, 700)),
+                                        ("bf16", (1024, 1024)), ("bf16", (64, 64)),
+                                        ("fp32", (129, 1000))])
+def test_cta_pair_tiles_match(ctx, prec, shape, fuse):
+    """256 x 256 tiles on CTA pairs (tcgen05 cta_group::2) give the result of
+    128 x 256 tiles on single CTAs, in the fused launch and launch by launch."""
+    a = _gap_matrix(*shape, seed=shape[0] * 3 + shape[1])
+    dev = torch.from_numpy(a).cuda()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    y2 = ctx.polar(dev, 0.3, iters=20, prec=prec, fuse=fuse, tile=512, status=status)
+    y1 = ctx.polar(dev, 0.3, iters=20, prec=prec, fuse=True, tile=256)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert oracle.relerr(y2.cpu().numpy(), y1.cpu().numpy()) < 1e-5
+    exact = oracle.svt_definition(a.astype(np.float64), 0.3)
+    assert oracle.relerr(y2.cpu().numpy(), exact) < TOL[prec]
+
+
+def test_invalid_tile_rejected(ctx):
+    dev = torch.zeros(8, 8, device="cuda")
+    with pytest.raises(pkg.SVTError):
+        ctx.polar(dev, 0.1, tile=300)
