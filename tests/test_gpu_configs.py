@@ -100,3 +100,67 @@ def test_error_curves_marchenko_pastur(ctx):
         assert abs(table[(tau, 4)]["fp32"] - table[(tau, 4)]["model"]) < 0.05 * table[(tau, 4)]["model"]
     # worse for tau near sigma_max (about 2 here) than near sigma_min
     assert table[(1.5, 20)]["bf16"] > table[(0.25, 20)]["bf16"]
+
+
+def _quarter_circle_quantiles(n):
+    """Singular values of an n x n N(0, 1/n) matrix follow the quarter-circle law
+    on [0, 2] (density sqrt(4 - s^2) / pi); returns its (i - 1/2) / n quantiles,
+    largest first, by bisection on the closed-form distribution function."""
+    cdf = lambda s: (s * np.sqrt(4.0 - s * s) / 2.0 + 2.0 * np.arcsin(s / 2.0)) / np.pi
+    p = (np.arange(n) + 0.5) / n
+    lo, hi = np.zeros(n), np.full(n, 2.0)
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        below = cdf(mid) < p
+        lo = np.where(below, mid, lo)
+        hi = np.where(below, hi, mid)
+    return np.ascontiguousarray(np.sort(0.5 * (lo + hi))[::-1])
+
+
+def test_error_curves_mp4096_known_spectrum(ctx):
+    """The benchmark's 4096^2 gap-free shape with a known SVD: sigma at the
+    quarter-circle quantiles (the Marchenko-Pastur law of the benchmark matrix),
+    Haar-random singular vectors, so A_tau is exact without a 4096^2 SVD. Error vs
+    tau and vs iterations for both tiers; the exact-arithmetic model is evaluated
+    on the singular values."""
+    n = 4096
+    sig = _quarter_circle_quantiles(n)
+    rng = np.random.default_rng(1002)
+    q1 = torch.linalg.qr(torch.from_numpy(rng.standard_normal((n, n))).cuda())[0]
+    q2 = torch.linalg.qr(torch.from_numpy(rng.standard_normal((n, n))).cuda())[0]
+    s_dev = torch.from_numpy(sig).cuda()
+    dev = ((q1 * s_dev) @ q2.T).float()
+    ctx.ensure_workspace(pkg.workspace_bytes(n, n, prec="fp32"))
+    taus = [0.25, 0.5, 1.0, 1.5]
+    ks = [4, 6, 8, 10, 12, 16, 20]
+    rows, table = [], {}
+    for tau in taus:
+        psi = np.maximum(sig - tau, 0.0)
+        exact = (q1 * torch.from_numpy(psi).cuda()) @ q2.T
+        nrm = torch.linalg.norm(exact).item()
+        for k in ks:
+            res = {}
+            for prec in ("bf16", "fp32"):
+                y = ctx.polar(dev, tau, iters=k, prec=prec)
+                torch.cuda.synchronize()
+                res[prec] = torch.linalg.norm(y.double() - exact).item() / nrm
+            coefs, _ = osch.pe5_schedule(k, 1e-3, 0.01)
+            phi = spectral.predicted_values(sig, tau, coefs, coefs, "gram", "gram")
+            res["model"] = float(np.linalg.norm(phi - psi) / np.linalg.norm(psi))
+            table[(tau, k)] = res
+            rows.append(f"| {tau} | {k} | {res['bf16']:.3e} | {res['fp32']:.3e} | {res['model']:.3e} |")
+    out = os.environ.get("SVT_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "error_curves_mp4096.md"), "w") as f:
+            f.write("| tau | iters | BF16 tier | FP32 tier | exact-arithmetic model |\n|---|---|---|---|---|\n")
+            f.write("\n".join(rows) + "\n")
+    for tau in taus:
+        assert all(np.isfinite(table[(tau, k)]["bf16"]) for k in ks)
+        # Section 3, Fig. 1: fast decay from 4 to 6 iterations, then a plateau
+        assert table[(tau, 6)]["bf16"] < 0.1 * table[(tau, 4)]["bf16"]
+        assert table[(tau, 20)]["bf16"] < 2.0 * table[(tau, 6)]["bf16"]
+        assert table[(tau, 20)]["fp32"] < 1e-3
+        assert table[(tau, 20)]["fp32"] < 0.1 * table[(tau, 20)]["bf16"]
+        assert abs(table[(tau, 4)]["fp32"] - table[(tau, 4)]["model"]) < 0.05 * table[(tau, 4)]["model"]
+    assert table[(1.5, 20)]["bf16"] > table[(0.25, 20)]["bf16"]
