@@ -180,7 +180,7 @@ def config(n):
     return {"workload": workload_name(n), "m": n, "n": n, "tau": TAU, "iters": ITERS,
             "precision": "bf16", "schedule": "pe5", "polish": True,
             "l2": "flushed between timed steps (512 MiB write outside the timed events)",
-            "tiles": "128x128 or 128x256 per product launch, chosen by svt_autotune",
+            "tiles": "one tile mode for the fused launch (128x128, 128x256 or CTA pairs on 256x256), chosen by svt_autotune from whole-solve timings",
             "parallelism": "replicas (independent matrices per GPU)"}
 
 

@@ -316,12 +316,14 @@ svt_status svt_ctx_profile_read(svt_ctx_t ctx, double *tc_ms, double *tc_flops,
                                 uint64_t *tc_launches);
 
 /*
- * Autotuner for the product kernel's tile width. Runs the svt_polar_ex solve of
- * this A (m x n, lda), tau and options (NULL = defaults) once as warm-up and `reps`
- * times timed, with 128 x 128 and with 128 x 256 tiles, times every product
- * launch with CUDA events on `stream`, and stores the faster width per launch in
- * the context. Later svt_polar / svt_polar_ex calls with the same shape and
- * options use the tuned widths. Y receives A_tau. Synchronises `stream`.
+ * Autotuner for the product kernel's tiles. Runs the svt_polar_ex solve of this A
+ * (m x n, lda), tau and options (NULL = defaults) with each tile mode (128 x 128,
+ * 128 x 256, and CTA pairs on 256 x 256), once as warm-up and `reps` times timed
+ * with CUDA events on `stream`. Fused solves (opt->fuse = 1, the default) keep the
+ * mode with the shortest whole solve; unfused solves keep the fastest mode per
+ * product launch. The choice is stored in the context; later svt_polar /
+ * svt_polar_ex calls with the same shape and options and tile = 0 use it. Y
+ * receives A_tau. Synchronises `stream`.
  * Errors: as svt_polar_ex; SVT_ERR_BUSY while serving requests are in flight.
  * The FP64 tier has no tile choice (returns SVT_OK without work).
  */

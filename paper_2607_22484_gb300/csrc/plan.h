@@ -116,17 +116,19 @@ struct TuneKey {
     int64_t m, n;
     int iters, prec, schedule, norm, polish, mode, hp_steps;
     double ell0, delta;
+    int fuse;
     bool operator<(const TuneKey &o) const
     {
-        return std::tie(m, n, iters, prec, schedule, norm, polish, mode, hp_steps, ell0, delta) <
+        return std::tie(m, n, iters, prec, schedule, norm, polish, mode, hp_steps, ell0, delta,
+                        fuse) <
                std::tie(o.m, o.n, o.iters, o.prec, o.schedule, o.norm, o.polish, o.mode,
-                        o.hp_steps, o.ell0, o.delta);
+                        o.hp_steps, o.ell0, o.delta, o.fuse);
     }
 };
 inline TuneKey tune_key(int64_t m, int64_t n, const Resolved &r)
 {
     return TuneKey{m, n, r.iters, r.prec, r.schedule, r.norm, r.polish, r.mode, r.hp_steps,
-                   r.ell0, r.delta};
+                   r.ell0, r.delta, r.fuse};
 }
 
 struct Key {

@@ -964,9 +964,26 @@ void evict_plans(svt_ctx *ctx, size_t max_entries)
     }
 }
 
+// Tile mode of a fused solve when none is requested or tuned, from whole-solve timings on
+// GB300 (BF16 tier, 20 steps): 128 x 128 tiles while the small side is at most ~2.5k
+// (more tiles per product keep all SMs busy: 1.35x at 1024^2, 1.16x at 2048^2, 1.07x at
+// 8192 x 2048), CTA pairs from ~32M elements on up (1.04-1.08x at 6144^2, 8192^2,
+// 16384 x 4096), 128 x 256 in between (3072^2, 4096^2).
+int fused_auto_width(int64_t m, int64_t n)
+{
+    const int64_t small = std::min(m, n);
+    if (small <= 2560)
+        return 128;
+    if (m * n >= (int64_t)32 << 20)
+        return kBnPair;
+    return 256;
+}
+
 svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_t ws_base,
                     size_t ws_avail, Plan **out, int force_bn, std::shared_ptr<Plan> *keep)
 {
+    if (force_bn == 0 && r.fuse && r.prec != SVT_FP64)
+        force_bn = fused_auto_width(m, n);
     Key k{m, n, r.iters, r.prec, r.schedule, r.norm, r.polish, r.mode, r.hp_steps, r.ell0, r.delta,
           ws_base, force_bn, r.fuse};
     auto it = ctx->plans.find(k);
@@ -1186,48 +1203,109 @@ svt_status svt_autotune(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int
         return SVT_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CallArgs a{A, lda, tau, Y, ldy, nullptr};
-    const int widths[2] = {128, 256};
-    Resolved rt = r;
-    rt.fuse = 0;  // launch-by-launch timing needs the unfused plan
-    std::vector<double> ms[2];
-    const bool prev_profile = ctx->profile;
-    for (int w = 0; w < 2; ++w) {
-        Plan *plan = nullptr;
-        st = get_plan(ctx, m, n, rt, 0, ctx->ws_bytes, &plan, widths[w]);
-        if (st != SVT_OK)
-            return st;
-        st = run_plan(ctx, *plan, a, s);  // warm-up
-        if (st != SVT_OK)
-            return st;
-        ctx->profile = true;
-        ctx->prof_pending.clear();
-        ctx->prof_next = 0;
-        for (int k = 0; k < reps; ++k) {
-            st = run_plan(ctx, *plan, a, s);
-            if (st != SVT_OK) {
-                ctx->profile = prev_profile;
-                return st;
-            }
+    const int widths[3] = {128, 256, kBnPair};
+    std::vector<int> choice;
+    if (r.fuse) {
+        // Fused solves: one width for all products; time whole solves with each.
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess)
+            return SVT_ERR_CUDA;
+        if (cudaEventCreate(&e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            return SVT_ERR_CUDA;
         }
-        const size_t per = plan->tc.size();
-        ms[w].assign(per, 0.0);
-        for (size_t i = 0; i < ctx->prof_pending.size(); ++i) {
-            auto &pr = ctx->prof_pending[i];
-            if (cudaEventSynchronize(pr.b) != cudaSuccess) {
-                ctx->profile = prev_profile;
-                return SVT_ERR_CUDA;
+        double best = -1.0;
+        int best_w = 0;
+        size_t n_tc = 0;
+        for (int w = 0; w < 3 && st == SVT_OK; ++w) {
+            Plan *plan = nullptr;
+            st = get_plan(ctx, m, n, r, 0, ctx->ws_bytes, &plan, widths[w]);
+            if (st != SVT_OK)
+                break;
+            if (!plan->fused)
+                continue;  // this width cannot run as one launch here
+            st = run_plan(ctx, *plan, a, s);  // warm-up
+            if (st != SVT_OK)
+                break;
+            cudaEventRecord(e0, s);
+            for (int k = 0; k < reps && st == SVT_OK; ++k)
+                st = run_plan(ctx, *plan, a, s);
+            cudaEventRecord(e1, s);
+            if (st != SVT_OK)
+                break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = SVT_ERR_CUDA;
+                break;
             }
             float t = 0.f;
-            cudaEventElapsedTime(&t, pr.a, pr.b);
-            ms[w][i % per] += t;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (best < 0.0 || t < best) {
+                best = t;
+                best_w = widths[w];
+                n_tc = plan->tc.size();
+            }
         }
-        ctx->prof_pending.clear();
-        ctx->prof_next = 0;
-        ctx->profile = prev_profile;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st != SVT_OK)
+            return st;
+        if (best_w == 0)
+            return SVT_OK;  // no width runs fused: keep the automatic choice
+        choice.assign(n_tc, best_w);
+    } else {
+        std::vector<double> ms[3];
+        const bool prev_profile = ctx->profile;
+        for (int w = 0; w < 3; ++w) {
+            Plan *plan = nullptr;
+            st = get_plan(ctx, m, n, r, 0, ctx->ws_bytes, &plan, widths[w]);
+            if (st != SVT_OK)
+                return st;
+            st = run_plan(ctx, *plan, a, s);  // warm-up
+            if (st != SVT_OK)
+                return st;
+            ctx->profile = true;
+            ctx->prof_pending.clear();
+            ctx->prof_next = 0;
+            for (int k = 0; k < reps; ++k) {
+                st = run_plan(ctx, *plan, a, s);
+                if (st != SVT_OK) {
+                    ctx->profile = prev_profile;
+                    return st;
+                }
+            }
+            const size_t per = plan->tc.size();
+            ms[w].assign(per, 0.0);
+            for (size_t i = 0; i < ctx->prof_pending.size(); ++i) {
+                auto &pr = ctx->prof_pending[i];
+                if (cudaEventSynchronize(pr.b) != cudaSuccess) {
+                    ctx->profile = prev_profile;
+                    return SVT_ERR_CUDA;
+                }
+                float t = 0.f;
+                cudaEventElapsedTime(&t, pr.a, pr.b);
+                ms[w][i % per] += t;
+            }
+            ctx->prof_pending.clear();
+            ctx->prof_next = 0;
+            ctx->profile = prev_profile;
+        }
+        choice.assign(ms[0].size(), 128);
+        for (size_t i = 0; i < choice.size(); ++i) {
+            int bw = 0;
+            for (int w = 1; w < 3; ++w)
+                if (ms[w][i] < ms[bw][i])
+                    bw = w;
+            choice[i] = widths[bw];
+        }
     }
-    std::vector<int> choice(ms[0].size());
-    for (size_t i = 0; i < choice.size(); ++i)
-        choice[i] = (ms[0][i] < ms[1][i]) ? 128 : 256;
+    // Plans built from an earlier tuning of this shape are stale.
+    for (auto it = ctx->plans.begin(); it != ctx->plans.end();) {
+        const Key &k = it->first;
+        if (k.force_bn < 0 && k.m == m && k.n == n && k.fuse == r.fuse)
+            it = ctx->plans.erase(it);
+        else
+            ++it;
+    }
     ctx->tuning[tune_key(m, n, r)] = choice;
     return SVT_OK;
 }
