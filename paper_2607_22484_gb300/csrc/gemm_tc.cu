@@ -29,6 +29,7 @@
 // other roles stop at their next wait, in-flight copies and MMAs are drained
 // (again with a bound) and tensor memory is released before the kernel returns.
 #include <algorithm>
+#include <cstddef>
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -466,67 +467,116 @@ __device__ __forceinline__ bool aligned16(const void *p)
     return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
 }
 
-// v[i] += beta * C(r, c0 + i) for i < ncol, vectorised where the row segment is
-// contiguous and its address (not just its offset) is 16-byte aligned.
-__device__ __forceinline__ void add_c32(const Epi &e, const void *cp0, int64_t ldc, int64_t r,
-                                        int64_t c0, int ncol, float beta, float *v)
+// The fields of the current problem that the epilogue reads for every 32 x 32
+// block, loaded once per change of problem into registers: the problem table
+// lives in global memory, and every memory-clobbering TMA or fence instruction
+// of the epilogue would otherwise force these loads to be repeated.
+struct EpiHot {
+    const void *c0, *c1;
+    void *o0, *o1, *t0, *t1;
+    const CUtensorMap *maps;  // mapO[0..1] then mapT[0..1] of the problem
+    double *norm_acc;
+    const double *diag, *dss;
+    int64_t ldc, ldo, ldt;
+    float alpha, beta, gamma;
+    int M, N, sym, otma, ttma, c_kind, c_trans, o_kind, o_trans, t_kind;
+};
+
+// Raw C values of one lane's 32-column row segment: BF16 hi in q[0..3] (lo of a
+// pair in q[4..7]) or FP32 in q[0..7].
+struct CRaw {
+    uint4 q[8];
+};
+
+// Issue the loads of C(r, c0 .. c0 + 31) into registers. Returns false where the
+// vector form does not apply (no C, row outside, transposed C, a ragged right edge,
+// or a row address that is not 16-byte aligned); c_apply then reads C directly.
+__device__ __forceinline__ bool c_load(const EpiHot &h, int64_t r, int64_t c0, bool full_row,
+                                       CRaw &cr)
 {
-    if (!e.c_trans) {
-        const int64_t off = r * ldc + c0;
-        if (ncol == 32 && (e.c_kind == C_BF16 || e.c_kind == C_PAIR) &&
-            aligned16(static_cast<const __nv_bfloat16 *>(cp0) + off) &&
-            (e.c_kind == C_BF16 || aligned16(static_cast<const __nv_bfloat16 *>(e.c1) + off))) {
-            const uint4 *h = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(cp0) + off);
-            const uint4 *l = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(e.c1) + off);
+    if (h.c_kind == C_NONE || h.c_trans || !full_row)
+        return false;
+    const int64_t off = r * h.ldc + c0;
+    if (h.c_kind == C_F32) {
+        const float *p = static_cast<const float *>(h.c0) + off;
+        if (!aligned16(p))
+            return false;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            cr.q[q] = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+        return true;
+    }
+    const __nv_bfloat16 *ph = static_cast<const __nv_bfloat16 *>(h.c0) + off;
+    const __nv_bfloat16 *pl = static_cast<const __nv_bfloat16 *>(h.c1) + off;
+    if (!aligned16(ph) || (h.c_kind == C_PAIR && !aligned16(pl)))
+        return false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        cr.q[q] = __ldg(reinterpret_cast<const uint4 *>(ph) + q);
+    if (h.c_kind == C_PAIR) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            cr.q[4 + q] = __ldg(reinterpret_cast<const uint4 *>(pl) + q);
+    }
+    return true;
+}
+
+// v[i] += beta * C(r, c0 + i) for i < ncol, from registers loaded by c_load (vec)
+// or read directly (any layout, alignment or edge).
+__device__ __forceinline__ void c_apply(const EpiHot &h, const CRaw &cr, bool vec, int64_t r,
+                                        int64_t c0, int ncol, bool row_ok, float *v)
+{
+    if (h.c_kind == C_NONE || !row_ok)
+        return;
+    const float beta = h.beta;
+    if (vec) {
+        if (h.c_kind == C_F32) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                v[4 * q] += beta * __uint_as_float(cr.q[q].x);
+                v[4 * q + 1] += beta * __uint_as_float(cr.q[q].y);
+                v[4 * q + 2] += beta * __uint_as_float(cr.q[q].z);
+                v[4 * q + 3] += beta * __uint_as_float(cr.q[q].w);
+            }
+            return;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&cr.q[q]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 f = __bfloat1622float2(b[j]);
+                v[q * 8 + 2 * j] += beta * f.x;
+                v[q * 8 + 2 * j + 1] += beta * f.y;
+            }
+        }
+        if (h.c_kind == C_PAIR) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                uint4 u = __ldg(h + q);
-                const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&u);
+                const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&cr.q[4 + q]);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    float2 f = __bfloat1622float2(b[j]);
+                    const float2 f = __bfloat1622float2(b[j]);
                     v[q * 8 + 2 * j] += beta * f.x;
                     v[q * 8 + 2 * j + 1] += beta * f.y;
                 }
-                if (e.c_kind == C_PAIR) {
-                    uint4 w = __ldg(l + q);
-                    const __nv_bfloat162 *d = reinterpret_cast<const __nv_bfloat162 *>(&w);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float2 f = __bfloat1622float2(d[j]);
-                        v[q * 8 + 2 * j] += beta * f.x;
-                        v[q * 8 + 2 * j + 1] += beta * f.y;
-                    }
-                }
             }
-            return;
         }
-        if (ncol == 32 && e.c_kind == C_F32 && aligned16(static_cast<const float *>(cp0) + off)) {
-            const float4 *f = reinterpret_cast<const float4 *>(static_cast<const float *>(cp0) + off);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float4 u = __ldg(f + q);
-                v[4 * q] += beta * u.x;
-                v[4 * q + 1] += beta * u.y;
-                v[4 * q + 2] += beta * u.z;
-                v[4 * q + 3] += beta * u.w;
-            }
-            return;
-        }
+        return;
     }
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
         if (i >= ncol)
             continue;
         const int64_t c = c0 + i;
-        const int64_t off = e.c_trans ? c * ldc + r : r * ldc + c;
+        const int64_t off = h.c_trans ? c * h.ldc + r : r * h.ldc + c;
         float x;
-        if (e.c_kind == C_F32)
-            x = static_cast<const float *>(cp0)[off];
+        if (h.c_kind == C_F32)
+            x = static_cast<const float *>(h.c0)[off];
         else {
-            x = __bfloat162float(static_cast<const __nv_bfloat16 *>(cp0)[off]);
-            if (e.c_kind == C_PAIR)
-                x += __bfloat162float(static_cast<const __nv_bfloat16 *>(e.c1)[off]);
+            x = __bfloat162float(static_cast<const __nv_bfloat16 *>(h.c0)[off]);
+            if (h.c_kind == C_PAIR)
+                x += __bfloat162float(static_cast<const __nv_bfloat16 *>(h.c1)[off]);
         }
         v[i] += beta * x;
     }
@@ -712,70 +762,62 @@ __device__ __forceinline__ void tma_store_block(const float *x, int kind, bool t
     }
 }
 
-// Epilogue of one 32 x 32 block: lane = tile row r (r0 + lane), columns c0 .. c0 + 31.
-// Values are computed in registers, staged in shared memory, then stored coalesced
-// to every requested destination: the output (row-major or transposed), the
-// extra transposed copy and, for symmetric products, the mirror.
-// Per-call fields of a grouped launch (C source, main output); the rest of the
-// epilogue comes from the problem.
-struct EpiOverride {
-    const void *c0;
-    int64_t ldc;
-    void *o0;
-    int64_t ldo;
-    int otma;
-};
-
-__device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiOverride &ov,
-                                               const EpiScales &s, int64_t r0, int64_t c0, float *v,
-                                               double &nrm, uint8_t *stg, int lane)
+// Rest of the epilogue of one 32 x 32 block after alpha D + beta C: the identity
+// term (or the FP64 shifted-Gram diagonal) on the diagonal, the squared-norm
+// contribution, then the stores. lane = tile row r0 + lane, columns c0 .. c0 + 31.
+// Values are staged in shared memory and stored coalesced to every requested
+// destination: the output (row-major or transposed), the extra transposed copy
+// and, for symmetric products, the mirror.
+__device__ __forceinline__ void epilogue_finish(const EpiHot &h, int64_t r0, int64_t c0, float *v,
+                                                double &nrm, uint8_t *stg, int lane)
 {
-    const Epi &e = P.ep;
-    const int p_otma = ov.otma;
     const int64_t r = r0 + lane;
-    const bool row_ok = r < P.M;
-    const int64_t rem = (int64_t)P.N - c0;
+    const bool row_ok = r < h.M;
+    const int64_t rem = (int64_t)h.N - c0;
     const int ncol = rem < 32 ? (int)rem : 32;
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-        v[i] *= s.alpha;
-    if (e.c_kind != C_NONE && row_ok)
-        add_c32(e, ov.c0, ov.ldc, r, c0, ncol, s.beta, v);
     const bool diag_block = (r0 == c0);
+    if (diag_block) {  // this lane's diagonal element is column i == lane
+        const bool dg = h.diag != nullptr;
+        const float dval = (dg && row_ok) ? (float)(h.diag[r] * h.dss[0] - h.dss[1]) : 0.f;
+        const float g = h.gamma;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        const int64_t c = c0 + i;
-        float x = v[i];
-        if (diag_block && r == c) {
-            x += s.gamma;
-            if (e.diag)
-                x = (float)(e.diag[r] * e.dss[0] - e.dss[1]);
-        }
-        if (e.norm_acc && row_ok && i < ncol && (!P.sym || r <= c)) {
-            const double xd = (double)x;
-            nrm += (P.sym && r != c) ? 2.0 * xd * xd : xd * xd;
-        }
-        v[i] = x;
+        for (int i = 0; i < 32; ++i)
+            if (i == lane)
+                v[i] = dg ? dval : v[i] + g;
     }
-    const bool symdiag = P.sym && diag_block;
+    if (h.norm_acc && row_ok) {
+        // FP32 within the row's 32 values (relative error <= 32 * 2^-24), FP64 across.
+        float acc = 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            float w = (i < ncol) ? 1.f : 0.f;
+            if (h.sym) {
+                const int64_t c = c0 + i;
+                w = (r < c) ? 2.f * w : (r == c ? w : 0.f);
+            }
+            acc = fmaf(w * v[i], v[i], acc);
+        }
+        nrm += (double)acc;
+    }
+    const bool symdiag = h.sym && diag_block;
     // FP32 blocks use the whole 4 KiB; BF16 hi/lo blocks 2 KiB each.
     uint8_t *stg0 = stg, *stg1 = stg + 2048;
     // Outputs through TMA stores (all but diagonal blocks of symmetric products).
-    const bool o_tma = p_otma && e.o_kind != O_NONE && !symdiag;
+    const bool o_tma = h.otma && h.o_kind != O_NONE && !symdiag;
     if (o_tma)
-        tma_store_block(v, e.o_kind, e.o_trans != 0, &P.mapO[0], &P.mapO[1], (int)r0, (int)c0,
+        tma_store_block(v, h.o_kind, h.o_trans != 0, &h.maps[0], &h.maps[1], (int)r0, (int)c0,
                         stg0, stg1, lane);
-    if (P.sym && !diag_block && p_otma)  // mirror of a block strictly above the diagonal
-        tma_store_block(v, e.o_kind, true, &P.mapO[0], &P.mapO[1], (int)r0, (int)c0, stg0, stg1,
+    if (h.sym && !diag_block && h.otma)  // mirror of a block strictly above the diagonal
+        tma_store_block(v, h.o_kind, true, &h.maps[0], &h.maps[1], (int)r0, (int)c0, stg0, stg1,
                         lane);
-    if (P.t_tma && e.t_kind != O_NONE)
-        tma_store_block(v, e.t_kind, true, &P.mapT[0], &P.mapT[1], (int)r0, (int)c0, stg0, stg1,
+    if (h.ttma && h.t_kind != O_NONE)
+        tma_store_block(v, h.t_kind, true, &h.maps[2], &h.maps[3], (int)r0, (int)c0, stg0, stg1,
                         lane);
-    const bool need_plain = (e.o_kind != O_NONE && !o_tma) || (P.sym && !diag_block && !p_otma) ||
-                            (e.t_kind != O_NONE && !P.t_tma);
+    const bool need_plain = (h.o_kind != O_NONE && !o_tma) || (h.sym && !diag_block && !h.otma) ||
+                            (h.t_kind != O_NONE && !h.ttma);
     if (!need_plain)
         return;
-    // Coalesced plain-store path: stage with a 33-float pitch, then whole row segments.
+    // Coalesced plain-store path: stage with a swizzled pitch, then whole row segments.
     if (lane == 0)
         bulk_wait_read0();
     __syncwarp();
@@ -784,13 +826,62 @@ __device__ __forceinline__ void epilogue_block(const TcProblem &P, const EpiOver
     for (int i = 0; i < 32; ++i)
         st[xs_idx(lane, i)] = v[i];
     __syncwarp();
-    if (e.o_kind != O_NONE && !o_tma)
-        store_block(st, e.o_kind, ov.o0, e.o1, ov.ldo, r0, c0, P.M, P.N, e.o_trans != 0, symdiag, lane);
-    if (P.sym && !diag_block && !p_otma)
-        store_block(st, e.o_kind, ov.o0, e.o1, ov.ldo, r0, c0, P.M, P.N, true, false, lane);
-    if (e.t_kind != O_NONE && !P.t_tma)
-        store_block(st, e.t_kind, e.t0, e.t1, e.ldt, r0, c0, P.M, P.N, true, false, lane);
+    if (h.o_kind != O_NONE && !o_tma)
+        store_block(st, h.o_kind, h.o0, h.o1, h.ldo, r0, c0, h.M, h.N, h.o_trans != 0, symdiag, lane);
+    if (h.sym && !diag_block && !h.otma)
+        store_block(st, h.o_kind, h.o0, h.o1, h.ldo, r0, c0, h.M, h.N, true, false, lane);
+    if (h.t_kind != O_NONE && !h.ttma)
+        store_block(st, h.t_kind, h.t0, h.t1, h.ldt, r0, c0, h.M, h.N, true, false, lane);
     __syncwarp();
+}
+
+// Load the epilogue fields of problem P (with the per-call fields of a grouped or
+// fused launch) into registers.
+__device__ __forceinline__ void load_hot(EpiHot &h, const TcProblem &P, const CallRec *calls)
+{
+    const Epi &e = P.ep;
+    h.c0 = e.c0;
+    h.c1 = e.c1;
+    h.ldc = e.ldc;
+    h.o0 = e.o0;
+    h.o1 = e.o1;
+    h.ldo = e.ldo;
+    h.t0 = e.t0;
+    h.t1 = e.t1;
+    h.ldt = e.ldt;
+    h.maps = &P.mapO[0];
+    h.norm_acc = e.norm_acc;
+    h.diag = e.diag;
+    h.dss = e.dss;
+    h.M = P.M;
+    h.N = P.N;
+    h.sym = P.sym;
+    h.otma = P.o_tma;
+    h.ttma = P.t_tma;
+    h.c_kind = e.c_kind;
+    h.c_trans = e.c_trans;
+    h.o_kind = e.o_kind;
+    h.o_trans = e.o_trans;
+    h.t_kind = e.t_kind;
+    double alpha = e.alpha;
+    if (P.patch) {  // grouped / fused launch: per-call fields
+        const CallRec &cr = calls[P.call_idx];
+        if (P.patch & PT_C_IS_A) {
+            h.c0 = cr.A;
+            h.ldc = cr.lda;
+        }
+        if (P.patch & PT_O_IS_Y) {
+            h.o0 = cr.Y;
+            h.ldo = cr.ldy;
+            h.otma = 0;
+        }
+        if (P.patch & PT_ALPHA_NEG_TAU)
+            alpha = -(double)cr.tau;
+    }
+    const EpiScales sc = epi_scales(e, alpha);
+    h.alpha = sc.alpha;
+    h.beta = sc.beta;
+    h.gamma = sc.gamma;
 }
 
 // --------------------------------------------------------------- kernel
@@ -1058,8 +1149,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         int buf = 0;
         uint32_t tphase = 0;
         int last_prob = -1;
-        EpiScales sc{1.f, 0.f, 0.f};
-        EpiOverride ov{nullptr, 0, nullptr, 0, 0};
+        EpiHot h;
         int ri = 0;
         uint32_t rphase = 0;
         for (int t = t_first;; t += t_step) {
@@ -1098,52 +1188,58 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 __syncwarp();
             }
             if (tc.prob != last_prob) {
-                ov.c0 = P.ep.c0;
-                ov.ldc = P.ep.ldc;
-                ov.o0 = P.ep.o0;
-                ov.ldo = P.ep.ldo;
-                ov.otma = P.o_tma;
-                double alpha = P.ep.alpha;
-                if (P.patch) {  // grouped / fused launch: per-call fields
-                    const CallRec &cr = calls[P.call_idx];
-                    if (P.patch & PT_C_IS_A) {
-                        ov.c0 = cr.A;
-                        ov.ldc = cr.lda;
-                    }
-                    if (P.patch & PT_O_IS_Y) {
-                        ov.o0 = cr.Y;
-                        ov.ldo = cr.ldy;
-                        ov.otma = 0;
-                    }
-                    if (P.patch & PT_ALPHA_NEG_TAU)
-                        alpha = -(double)cr.tau;
-                }
-                sc = epi_scales(P.ep, alpha);
+                load_hot(h, P, calls);
                 last_prob = tc.prob;
             }
+            const int64_t warp_row0 = (int64_t)tc.tm * kBM + quad * 32;
+            const int64_t row = warp_row0 + lane;
+            const bool row_ok = row < h.M;
+            // This warp's 32-column chunks: every other one, skipping chunks right of
+            // N or wholly below the diagonal (warp-uniform).
+            auto next_chunk = [&](int ch) {
+                for (; ch < BN / 32; ch += 2) {
+                    const int64_t c0 = (int64_t)tc.tn * BN + ch * 32;
+                    if (c0 < h.N && warp_row0 < h.M && !(h.sym && warp_row0 > c0 + 31))
+                        break;
+                }
+                return ch;
+            };
+            auto full_row = [&](int ch) {
+                return row_ok && (int64_t)h.N - ((int64_t)tc.tn * BN + ch * 32) >= 32;
+            };
+            int ch = next_chunk(half);
+            // The first chunk's C is loaded while the accumulator is still being computed.
+            CRaw cr;
+            bool cvec = false;
+            if (ch < BN / 32)
+                cvec = c_load(h, row, (int64_t)tc.tn * BN + ch * 32, full_row(ch), cr);
             if (!wait_bar<PAIR>(&tfull[buf], tphase, abort_flag, status0, kWaitTimeoutNs))
                 break;
             tc_fence_after();
-            const int64_t warp_row0 = (int64_t)tc.tm * kBM + quad * 32;
             double nrm = 0.0;
 #pragma unroll 1
-            for (int ch = half; ch < BN / 32; ch += 2) {
+            while (ch < BN / 32) {
+                const int nx = next_chunk(ch + 2);
                 const int64_t c0 = (int64_t)tc.tn * BN + ch * 32;
-                // Warp-uniform skips: chunk right of N, or wholly below the diagonal.
-                if (c0 >= P.N || warp_row0 >= P.M)
-                    continue;
-                if (P.sym && warp_row0 > c0 + 31)
-                    continue;
+                const int64_t rem = (int64_t)h.N - c0;
                 float v[32];
                 tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + ch * 32), v);
-                epilogue_block(P, ov, sc, warp_row0, c0, v, nrm, stage_buf, lane);
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    v[i] *= h.alpha;
+                c_apply(h, cr, cvec, row, c0, rem < 32 ? (int)rem : 32, row_ok, v);
+                // The next chunk's C is in flight while this chunk is stored.
+                if (nx < BN / 32)
+                    cvec = c_load(h, row, (int64_t)tc.tn * BN + nx * 32, full_row(nx), cr);
+                epilogue_finish(h, warp_row0, c0, v, nrm, stage_buf, lane);
+                ch = nx;
             }
-            if (P.ep.norm_acc) {
+            if (h.norm_acc) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1)
                     nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
                 if (lane == 0 && nrm != 0.0)
-                    atomicAdd(P.ep.norm_acc, nrm);
+                    atomicAdd(h.norm_acc, nrm);
             }
             tc_fence_before();
             if (PAIR) {
@@ -1187,6 +1283,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         tmem_dealloc<PAIR>(tmem_base, 2 * BN);
     }
 }
+
+static_assert(offsetof(TcProblem, mapT) == offsetof(TcProblem, mapO) + 2 * sizeof(CUtensorMap),
+              "the epilogue addresses mapO[0..1] and mapT[0..1] as one array");
 
 template <int BN, int STAGES, bool PAIR>
 constexpr int smem_bytes()

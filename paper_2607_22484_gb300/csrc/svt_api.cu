@@ -965,18 +965,13 @@ void evict_plans(svt_ctx *ctx, size_t max_entries)
 }
 
 // Tile mode of a fused solve when none is requested or tuned, from whole-solve timings on
-// GB300 (BF16 tier, 20 steps): 128 x 128 tiles while the small side is at most ~2.5k
-// (more tiles per product keep all SMs busy: 1.35x at 1024^2, 1.16x at 2048^2, 1.07x at
-// 8192 x 2048), CTA pairs from ~32M elements on up (1.04-1.08x at 6144^2, 8192^2,
-// 16384 x 4096), 128 x 256 in between (3072^2, 4096^2).
+// GB300 (BF16 tier, 20 steps): 128 x 128 tiles while the small side is at most 1536 (more
+// tiles per product keep all SMs busy: 1.31x over 128 x 256 at 1024^2), CTA pairs above
+// (1.01x at 2048^2, 1.035x at 3072^2 and 4096^2, 1.04x at 8192 x 2048, 1.08x at 6144^2,
+// 8192^2 and 16384 x 4096).
 int fused_auto_width(int64_t m, int64_t n)
 {
-    const int64_t small = std::min(m, n);
-    if (small <= 2560)
-        return 128;
-    if (m * n >= (int64_t)32 << 20)
-        return kBnPair;
-    return 256;
+    return std::min(m, n) <= 1536 ? 128 : kBnPair;
 }
 
 svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_t ws_base,
