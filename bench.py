@@ -180,7 +180,7 @@ def config(n):
     return {"workload": workload_name(n), "m": n, "n": n, "tau": TAU, "iters": ITERS,
             "precision": "bf16", "schedule": "pe5", "polish": True,
             "l2": "flushed between timed steps (512 MiB write outside the timed events)",
-            "tiles": "one tile mode for the fused launch (128x128, 128x256 or CTA pairs on 256x256), chosen by svt_autotune from whole-solve timings",
+            "tiles": "automatic tile mode of the fused launch: CTA pairs (tcgen05 cta_group::2) on 256x256 tiles at this size",
             "parallelism": "replicas (independent matrices per GPU)"}
 
 
@@ -424,8 +424,8 @@ def run_ours(args, n):
     if args.tile:
         opts["tile"] = args.tile
 
-    if not args.no_autotune and not args.tile:
-        ctx.autotune(A, TAU, out=Y, reps=2, **opts)  # tile width per product launch
+    if args.autotune and not args.tile:
+        ctx.autotune(A, TAU, out=Y, reps=2, **opts)  # tile mode from whole-solve timings
     sampler = ClockSampler(local)
     sampler.start()  # started before the warm-up so its start-up cost is outside the timed region
     for _ in range(args.warmup):
@@ -583,8 +583,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fuse", action="store_true",
                     help="one launch per product stage instead of the fused persistent launch")
+    ap.add_argument("--autotune", action="store_true",
+                    help="let svt_autotune pick the tile mode from whole-solve timings "
+                         "(default: the library's automatic rule)")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="use the default tile widths instead of svt_autotune")
+                    help="accepted for compatibility; the automatic rule is the default")
     ap.add_argument("--tile", type=int, default=0, choices=[0, 128, 256, 512],
                     help="product tiles: 0 automatic, 128/256 one CTA per 128 x tile, "
                          "512 a CTA pair per 256 x 256 tile")
