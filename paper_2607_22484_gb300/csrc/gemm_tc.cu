@@ -221,6 +221,12 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int 
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// At most N of this thread's most recent bulk groups may still be reading shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ void bulk_wait_all0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
@@ -397,21 +403,33 @@ __device__ __forceinline__ const TcProblem &prob_at(const TcLaunch &L, int p)
 // Dense problems: column-major over the tile grid. Symmetric problems: only
 // tiles holding some element with row <= col; column tn holds r (tn + 1) row
 // tiles (r = BN / TM), so the first tile of column tn is r tn (tn + 1) / 2.
+// A role's tile indices only increase, so the problem search gallops forward from
+// the previous answer (`hint`) instead of bisecting the whole table: a few
+// dependent loads of the tile prefix sums instead of log2(problems).
 template <int BN, int TM>
-__device__ TileCoord decode_tile(const TcLaunch &L, int t)
+__device__ TileCoord decode_tile(const TcLaunch &L, int t, int &hint)
 {
     TileCoord tc{0, 0, 0, false};
     int p = 0, start = 0;
     if (L.gtab) {
-        int lo = 0, hi = L.gcount - 1;  // last p with gstart[p] <= t
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
+        p = hint;
+        if (p < 0 || p >= L.gcount || L.gstart[p] > t)
+            p = 0;
+        int step = 1, q = p + 1;  // first q > p with gstart[q] > t lies in (p, q]
+        while (q < L.gcount && L.gstart[q] <= t) {
+            p = q;
+            step <<= 1;
+            q = p + step;
+        }
+        int hi = (q < L.gcount ? q : L.gcount) - 1;  // last p with gstart[p] <= t
+        while (p < hi) {
+            const int mid = (p + hi + 1) >> 1;
             if (L.gstart[mid] <= t)
-                lo = mid;
+                p = mid;
             else
                 hi = mid - 1;
         }
-        p = lo;
+        hint = p;
         start = L.gstart[p];
     } else {
         while (p + 1 < L.nprob && t >= L.tile_start[p + 1])
@@ -697,17 +715,23 @@ __device__ __forceinline__ uint32_t stg_off_b16(int row, int col)
 }
 
 // Stage the warp's 32 x 32 block (lane = block row, x[] = its 32 columns) and
-// store it with one or two TMA stores: at tile coordinates (x = c0, y = r0), or
-// transposed at (x = r0, y = c0). `kind` is O_F32, O_BF16 or O_PAIR (hi through
-// m0, lo through m1). stg0 is this warp's 1024-byte aligned staging buffer (4 KiB
-// for FP32); for BF16 blocks stg0 and stg1 = stg0 + 2 KiB hold hi and lo.
+// store it with one or two TMA stores (one bulk group): at tile coordinates
+// (x = c0, y = r0), or transposed at (x = r0, y = c0). `kind` is O_F32, O_BF16 or
+// O_PAIR (hi through m0, lo through m1). The warp owns NSTG 4 KiB staging slots
+// (1024-byte aligned) used in turn, so a store's shared-memory read overlaps the
+// staging of the next NSTG - 1 blocks; an FP32 block fills a slot, BF16 hi and lo
+// take its two halves.
+template <int NSTG>
 __device__ __forceinline__ void tma_store_block(const float *x, int kind, bool trans,
                                                 const CUtensorMap *m0, const CUtensorMap *m1,
-                                                int r0, int c0, uint8_t *stg0, uint8_t *stg1,
+                                                int r0, int c0, uint8_t *stg_base, int &slot,
                                                 int lane)
 {
+    uint8_t *stg0 = stg_base + slot * 4096, *stg1 = stg0 + 2048;
+    if (++slot == NSTG)
+        slot = 0;
     if (lane == 0)
-        bulk_wait_read0();  // previous stores from these buffers have read them
+        bulk_wait_read<NSTG - 1>();  // the store that last used this slot has read it
     __syncwarp();
     if (kind == O_F32) {
         if (!trans) {
@@ -768,8 +792,9 @@ __device__ __forceinline__ void tma_store_block(const float *x, int kind, bool t
 // Values are staged in shared memory and stored coalesced to every requested
 // destination: the output (row-major or transposed), the extra transposed copy
 // and, for symmetric products, the mirror.
+template <int NSTG>
 __device__ __forceinline__ void epilogue_finish(const EpiHot &h, int64_t r0, int64_t c0, float *v,
-                                                double &nrm, uint8_t *stg, int lane)
+                                                double &nrm, uint8_t *stg, int &slot, int lane)
 {
     const int64_t r = r0 + lane;
     const bool row_ok = r < h.M;
@@ -800,19 +825,17 @@ __device__ __forceinline__ void epilogue_finish(const EpiHot &h, int64_t r0, int
         nrm += (double)acc;
     }
     const bool symdiag = h.sym && diag_block;
-    // FP32 blocks use the whole 4 KiB; BF16 hi/lo blocks 2 KiB each.
-    uint8_t *stg0 = stg, *stg1 = stg + 2048;
     // Outputs through TMA stores (all but diagonal blocks of symmetric products).
     const bool o_tma = h.otma && h.o_kind != O_NONE && !symdiag;
     if (o_tma)
-        tma_store_block(v, h.o_kind, h.o_trans != 0, &h.maps[0], &h.maps[1], (int)r0, (int)c0,
-                        stg0, stg1, lane);
+        tma_store_block<NSTG>(v, h.o_kind, h.o_trans != 0, &h.maps[0], &h.maps[1], (int)r0,
+                              (int)c0, stg, slot, lane);
     if (h.sym && !diag_block && h.otma)  // mirror of a block strictly above the diagonal
-        tma_store_block(v, h.o_kind, true, &h.maps[0], &h.maps[1], (int)r0, (int)c0, stg0, stg1,
-                        lane);
+        tma_store_block<NSTG>(v, h.o_kind, true, &h.maps[0], &h.maps[1], (int)r0, (int)c0, stg,
+                              slot, lane);
     if (h.ttma && h.t_kind != O_NONE)
-        tma_store_block(v, h.t_kind, true, &h.maps[2], &h.maps[3], (int)r0, (int)c0, stg0, stg1,
-                        lane);
+        tma_store_block<NSTG>(v, h.t_kind, true, &h.maps[2], &h.maps[3], (int)r0, (int)c0, stg,
+                              slot, lane);
     const bool need_plain = (h.o_kind != O_NONE && !o_tma) || (h.sym && !diag_block && !h.otma) ||
                             (h.t_kind != O_NONE && !h.ttma);
     if (!need_plain)
@@ -888,7 +911,7 @@ __device__ __forceinline__ void load_hot(EpiHot &h, const TcProblem &P, const Ca
 
 constexpr int kRingTiles = 4;  // fused launches: tile ids in flight between the roles
 
-template <int BN, int STAGES, bool CHAIN, bool PAIR>
+template <int BN, int STAGES, bool CHAIN, bool PAIR, int NSTG>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcLaunch L)
 {
     static_assert(!PAIR || BN == 256, "CTA pairs compute 256 x 256 tiles");
@@ -901,8 +924,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     constexpr int TILE_ROWS = PAIR ? 2 * kBM : kBM;
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * A_BYTES;
-    uint8_t *stage_all = sB + STAGES * B_BYTES;  // kEpiWarps x 4 KiB, 1024-aligned
-    uint64_t *full = reinterpret_cast<uint64_t *>(stage_all + kEpiWarps * 4096);
+    uint8_t *stage_all = sB + STAGES * B_BYTES;  // kEpiWarps x NSTG x 4 KiB, 1024-aligned
+    uint64_t *full = reinterpret_cast<uint64_t *>(stage_all + kEpiWarps * NSTG * 4096);
     uint64_t *empty = full + STAGES;
     uint64_t *tfull = empty + STAGES;
     uint64_t *tempty = tfull + 2;
@@ -914,6 +937,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     uint64_t *rfull = reinterpret_cast<uint64_t *>(
         (reinterpret_cast<uintptr_t>(tmem_slot + 3) + 7) & ~static_cast<uintptr_t>(7));
     uint64_t *rempty = rfull + kRingTiles;
+    // Ring entry i: tring[4 i .. 4 i + 3] = tile index (-1: no more tiles), problem
+    // (-1: nothing to compute), tile row, tile column -- decoded once by the producer.
     volatile int *tring = reinterpret_cast<volatile int *>(rempty + kRingTiles);
     const CallRec *calls = L.calls ? L.calls : &L.call_inline;
 
@@ -972,25 +997,40 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         bool ok = true;
         int ri = 0;
         uint32_t rphase = 0;
+        int hint = 0;
         for (int t = t_first; ok; t += t_step) {
+            TileCoord tc;
             if (CHAIN) {
                 if (!PAIR || leader) {
-                    // Take the next tile in table order and hand its id to the other roles.
+                    // Take the next tile in table order, decode it and hand it to the
+                    // other roles (and to the peer CTA of a pair).
                     if (!wait_bar<PAIR>(&rempty[ri], rphase ^ 1u, abort_flag, status0, kWaitTimeoutNs))
                         break;
                     t = atomicAdd(L.tile_counter, 1);
                     t = (t < total) ? t : -1;
-                    tring[ri] = t;
+                    tc = TileCoord{-1, 0, 0, false};
+                    if (t >= 0)
+                        tc = decode_tile<BN, TILE_ROWS>(L, t, hint);
+                    const int ent[4] = {t, tc.valid ? tc.prob : -1, tc.tm, tc.tn};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        tring[4 * ri + k] = ent[k];
                     if (PAIR) {
-                        st_remote_u32(peer_addr((const void *)&tring[ri], 1), t);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            st_remote_u32(peer_addr((const void *)&tring[4 * ri + k], 1), ent[k]);
                         mbar_arrive_remote(peer_addr(&rfull[ri], 1));
                     }
                     mbar_arrive(&rfull[ri]);
                 } else {
-                    // Peer CTA: the leader's tile id.
+                    // Peer CTA: the leader's tile.
                     if (!mbar_wait_cluster(&rfull[ri], rphase, abort_flag, status0, kWaitTimeoutNs))
                         break;
-                    t = tring[ri];
+                    t = tring[4 * ri];
+                    tc.prob = tring[4 * ri + 1];
+                    tc.tm = tring[4 * ri + 2];
+                    tc.tn = tring[4 * ri + 3];
+                    tc.valid = tc.prob >= 0;
                     mbar_arrive_remote(peer_addr(&rempty[ri], 0));
                 }
                 if (++ri == kRingTiles) {
@@ -999,10 +1039,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 }
                 if (t < 0)
                     break;
-            } else if (t >= total) {
-                break;
+            } else {
+                if (t >= total)
+                    break;
+                tc = decode_tile<BN, TILE_ROWS>(L, t, hint);
             }
-            TileCoord tc = decode_tile<BN, TILE_ROWS>(L, t);
             if (!tc.valid)
                 continue;
             const TcProblem &P = prob_at(L, tc.prob);
@@ -1069,11 +1110,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         bool ok = true;
         int ri = 0;
         uint32_t rphase = 0;
+        int hint = 0;
         for (int t = t_first; ok; t += t_step) {
+            TileCoord tc;
             if (CHAIN) {
                 if (!mbar_wait(&rfull[ri], rphase, abort_flag, status0, kWaitTimeoutNs))
                     break;
-                t = tring[ri];
+                t = tring[4 * ri];
+                tc.prob = tring[4 * ri + 1];
+                tc.tm = tring[4 * ri + 2];
+                tc.tn = tring[4 * ri + 3];
+                tc.valid = tc.prob >= 0;
                 mbar_arrive(&rempty[ri]);
                 if (++ri == kRingTiles) {
                     ri = 0;
@@ -1081,10 +1128,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 }
                 if (t < 0)
                     break;
-            } else if (t >= total) {
-                break;
+            } else {
+                if (t >= total)
+                    break;
+                tc = decode_tile<BN, TILE_ROWS>(L, t, hint);
             }
-            TileCoord tc = decode_tile<BN, TILE_ROWS>(L, t);
             if (!tc.valid)
                 continue;
             const TcProblem &P = prob_at(L, tc.prob);
@@ -1145,18 +1193,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         // ------------------------------------------------ epilogue
         const int quad = warp & 3;  // TMEM lane quadrant this warp may access
         const int half = (warp - 2) >> 2;  // two warps per quadrant split the column chunks
-        uint8_t *stage_buf = stage_all + (warp - 2) * 4096;
+        uint8_t *stage_buf = stage_all + (warp - 2) * NSTG * 4096;
+        int slot = 0;  // next staging slot of this warp
         int buf = 0;
         uint32_t tphase = 0;
         int last_prob = -1;
         EpiHot h;
         int ri = 0;
         uint32_t rphase = 0;
+        int hint = 0;
         for (int t = t_first;; t += t_step) {
+            TileCoord tc;
             if (CHAIN) {
                 if (!wait_bar<PAIR>(&rfull[ri], rphase, abort_flag, status0, kWaitTimeoutNs))
                     break;
-                t = tring[ri];
+                t = tring[4 * ri];
+                tc.prob = tring[4 * ri + 1];
+                tc.tm = tring[4 * ri + 2];
+                tc.tn = tring[4 * ri + 3];
+                tc.valid = tc.prob >= 0;
                 __syncwarp();
                 if (lane == 0) {
                     if (PAIR && !leader)
@@ -1170,10 +1225,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 }
                 if (t < 0)
                     break;
-            } else if (t >= total) {
-                break;
+            } else {
+                if (t >= total)
+                    break;
+                tc = decode_tile<BN, TILE_ROWS>(L, t, hint);
             }
-            TileCoord tc = decode_tile<BN, TILE_ROWS>(L, t);
             if (!tc.valid)
                 continue;
             if (PAIR)
@@ -1231,7 +1287,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 // The next chunk's C is in flight while this chunk is stored.
                 if (nx < BN / 32)
                     cvec = c_load(h, row, (int64_t)tc.tn * BN + nx * 32, full_row(nx), cr);
-                epilogue_finish(h, warp_row0, c0, v, nrm, stage_buf, lane);
+                epilogue_finish<NSTG>(h, warp_row0, c0, v, nrm, stage_buf, slot, lane);
                 ch = nx;
             }
             if (h.norm_acc) {
@@ -1287,22 +1343,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 static_assert(offsetof(TcProblem, mapT) == offsetof(TcProblem, mapO) + 2 * sizeof(CUtensorMap),
               "the epilogue addresses mapO[0..1] and mapT[0..1] as one array");
 
-template <int BN, int STAGES, bool PAIR>
+template <int BN, int STAGES, bool PAIR, int NSTG>
 constexpr int smem_bytes()
 {
     return STAGES * (kBM + (PAIR ? BN / 2 : BN)) * kBK * 2 +
-           kEpiWarps * 4096 /* epilogue staging */ + 1024 /* alignment slack */ +
+           kEpiWarps * NSTG * 4096 /* epilogue staging */ + 1024 /* alignment slack */ +
            512 /* barriers, tile ring */;
 }
 
 // One launch of the product kernel over total_tiles tiles (tile-width code's
 // tiles: CTA pairs for kBnPair). Persistent: at most one CTA (pair) per SM (pair).
-template <int BN, int STAGES, bool CHAIN, bool PAIR>
+template <int BN, int STAGES, bool CHAIN, bool PAIR, int NSTG>
 cudaError_t launch_kernel(const TcLaunch &l, int total_tiles, int num_sms, cudaStream_t s)
 {
-    constexpr int smem = smem_bytes<BN, STAGES, PAIR>();
+    constexpr int smem = smem_bytes<BN, STAGES, PAIR, NSTG>();
     static_assert(smem <= 232448, "shared memory per CTA");
-    auto kern = tc_gemm_kernel<BN, STAGES, CHAIN, PAIR>;
+    auto kern = tc_gemm_kernel<BN, STAGES, CHAIN, PAIR, NSTG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess)
         return e;
@@ -1342,12 +1398,15 @@ cudaError_t launch_kernel(const TcLaunch &l, int total_tiles, int num_sms, cudaS
 template <bool CHAIN>
 cudaError_t launch_width(const TcLaunch &l, int bn, int total_tiles, int num_sms, cudaStream_t s)
 {
+    // 128 x 128 tiles serve small problems (short K): 5 stages and two staging slots
+    // per epilogue warp, so that stores overlap; the wide tiles keep every byte for
+    // pipeline stages.
     if (bn == 256)
-        return launch_kernel<256, 4, CHAIN, false>(l, total_tiles, num_sms, s);
+        return launch_kernel<256, 4, CHAIN, false, 1>(l, total_tiles, num_sms, s);
     if (bn == 128)
-        return launch_kernel<128, 6, CHAIN, false>(l, total_tiles, num_sms, s);
+        return launch_kernel<128, 5, CHAIN, false, 2>(l, total_tiles, num_sms, s);
     if (bn == kBnPair)
-        return launch_kernel<256, 6, CHAIN, true>(l, total_tiles, num_sms, s);
+        return launch_kernel<256, 6, CHAIN, true, 1>(l, total_tiles, num_sms, s);
     return cudaErrorInvalidValue;
 }
 
