@@ -309,11 +309,62 @@ def completion_extra(ctx_cls, pkg, torch, dev, steps=100, svd_steps=10):
             "speedup_per_step_vs_torch_svd": (ms_svd / svd_steps) / (ms / steps)}
 
 
+def shapes_extra(ctx_cls, pkg, torch, dev):
+    """The paper's other configurations, one solve at a time (CUDA events):
+    64x64 with a 6 % gap around tau = 0.3 (FP32 tier, 30 cubic Newton-Schulz steps, and
+    BF16 tier, 20 steps), and 8192 x 2048 / 2048 x 8192 rank-64 + 0.01 noise, tau = 0.5
+    (BF16 tier, SVT and Corollary 1 rank-r mode)."""
+    import svt_workloads as wl
+    out = {}
+    ctx = ctx_cls(dev.index or 0, workspace_bytes=1 << 20)
+
+    def timed(A, tau, reps, **opts):
+        Y = torch.empty_like(A)
+        for _ in range(3):
+            ctx.polar(A, tau, out=Y, **opts)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(True), torch.cuda.Event(True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record()
+            ctx.polar(A, tau, out=Y, **opts)
+            b.record()
+        torch.cuda.synchronize()
+        ms = sorted(a.elapsed_time(b) for a, b in ev)
+        return {"p50_ms": ms[len(ms) // 2], "p99_ms": ms[min(len(ms) - 1, int(0.99 * len(ms)))],
+                "solves_per_s": 1e3 * reps / sum(ms)}
+
+    a64 = torch.from_numpy(wl.spectrum_64()).to(dev)
+    out["64x64_fp32_ns3_30"] = timed(a64, 0.3, 200, iters=30, prec="fp32", schedule="ns3")
+    out["64x64_bf16_pe5_20"] = timed(a64, 0.3, 200, iters=ITERS, prec="bf16")
+    for (m, n) in ((8192, 2048), (2048, 8192)):
+        a = torch.from_numpy(wl.low_rank_plus_noise(m, n, 64, seed=1003)).to(dev)
+        out[f"{m}x{n}_bf16"] = timed(a, 0.5, 20, iters=ITERS, prec="bf16")
+        out[f"{m}x{n}_bf16_rank_r"] = timed(a, 0.5, 20, iters=ITERS, prec="bf16", mode="rank_r")
+    return out
+
+
+def svd_context(torch, A, tau, reps=2):
+    """Context only: SVT by torch.linalg.svd (FP32) on the benchmark matrix."""
+    def svt():
+        U, S, Vh = torch.linalg.svd(A, full_matrices=False)
+        return (U * torch.clamp(S - tau, min=0.0)) @ Vh
+    svt()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record()
+    for _ in range(reps):
+        svt()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def serving_extra(ctx_cls, pkg, torch, dev, n_req=200):
     """Poisson stream through svt_serve_submit / svt_serve_poll: sizes log-uniform
     256-8192 (rounded to powers of two), aspect 1, 2, 1/2, 30 % FP32 tier. Capacity
-    is the closed-loop throughput of the same stream; open-loop runs at 0.5, 0.8
-    and 0.95 of it report p50 / p99 submit-to-completion latency."""
+    is the closed-loop throughput of the same stream (at most 64 requests in flight);
+    open-loop runs at 0.5, 0.8 and 0.95 of it report p50 / p99 submit-to-completion
+    latency."""
     import math as _m
     import svt_workloads as wl
     reqs = wl.poisson_requests(n_req, rate_per_s=1.0)
@@ -340,14 +391,16 @@ def serving_extra(ctx_cls, pkg, torch, dev, n_req=200):
         ys.append(y)
         return y
 
-    def run(arrivals):
+    def run(arrivals, window=64):
+        """arrivals None: closed loop with at most `window` requests in flight."""
         import time as _t
         t0 = _t.perf_counter()
         pending, lat, busy, failed = {}, [], set(), 0
         i = 0
         while i < len(plan) or pending:
             now = _t.perf_counter() - t0
-            while i < len(plan) and (arrivals is None or arrivals[i] <= now):
+            while i < len(plan) and ((arrivals is None and len(pending) < window) or
+                                     (arrivals is not None and arrivals[i] <= now)):
                 key, tier = plan[i]
                 a, tau, _ = pool[key]
                 y = out_for(key, busy)
@@ -561,8 +614,10 @@ def run_ours(args, n):
     }
     if world == 1 and not args.no_extras:
         line["batch"] = batch_extra(pkg.Context, pkg, torch, dev)
-        line["serving"] = serving_extra(pkg.Context, pkg, torch, dev)
+        line["serving"] = serving_extra(pkg.Context, pkg, torch, dev, n_req=args.serve_requests)
         line["completion"] = completion_extra(pkg.Context, pkg, torch, dev)
+        line["shapes"] = shapes_extra(pkg.Context, pkg, torch, dev)
+        line["vs_fp32"]["torch_linalg_svd_svt_ms"] = svd_context(torch, A, TAU)
     if world == 1 and not args.no_cpu_baseline:
         est, desc, cores = oracle_sample(n, 1002, 96, repeats=1)
         line["cpu_baseline"] = {"value": 1.0 / est[0], "unit": "solves/s", "cores": cores,
@@ -591,6 +646,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0, choices=[0, 128, 256, 512],
                     help="product tiles: 0 automatic, 128/256 one CTA per 128 x tile, "
                          "512 a CTA pair per 256 x 256 tile")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests per serving run (the serving configuration asks for 10^4)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batch and serving measurements")
     ap.add_argument("--only-timed", action="store_true",

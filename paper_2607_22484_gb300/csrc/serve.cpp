@@ -824,11 +824,13 @@ void serve_shutdown(svt_ctx *ctx)
             cudaEventDestroy(s->ring_ev[i]);
     if (s->h_ring)
         cudaFreeHost(s->h_ring);
+    // Every request lives in `tickets` from submission until its release (queued and
+    // active ones included), so the ticket map owns them all.
+    s->queue.clear();
+    s->active.clear();
     for (auto &kv : s->tickets)
         delete kv.second;
-    for (Request *r : s->queue)
-        if (!s->tickets.count(r->ticket))
-            delete r;
+    s->tickets.clear();
     delete s;
     ctx->serve = nullptr;
 }

@@ -179,3 +179,26 @@ def test_serving_plan_cache_churn():
         exact, (u, s, v) = oracle.svt_definition(a.astype(np.float64), tau, return_svd=True)
         if oracle.gap(s, tau) >= 0.05:
             assert oracle.relerr(Y.cpu().numpy(), exact) < 2e-2
+
+
+def test_destroy_with_requests_queued_and_in_flight():
+    """svt_ctx_destroy while requests are still queued or running: the serving thread
+    stops, in-flight work is waited for, every request is freed exactly once, and the
+    process carries on (a second context solves normally)."""
+    items = _items(24, s_hi=512, seed=51)
+    need = max(pkg.workspace_bytes(it.m, it.n, prec="bf16") for it in items)
+    ctx = pkg.Context(0, workspace_bytes=2 * need)  # most requests wait for admission
+    keep = []
+    for it in items:
+        a = torch.from_numpy(it.matrix()).cuda()
+        y = torch.empty_like(a)
+        keep.append((a, y))
+        ctx.submit(a, it.tau, y, iters=20, prec="bf16")
+    ctx.close()
+    torch.cuda.synchronize()
+    it = items[0]
+    a = torch.from_numpy(it.matrix()).cuda()
+    fresh = pkg.Context(0, workspace_bytes=need)
+    y = fresh.polar(a, it.tau, iters=20, prec="bf16")
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(y).all())
