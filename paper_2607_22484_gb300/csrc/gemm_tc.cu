@@ -1388,7 +1388,8 @@ cudaError_t launch_kernel(const TcLaunch &l, int total_tiles, int num_sms, cudaS
             }
             max_pairs = nc;
         }
-        const int pairs = total_tiles < max_pairs ? total_tiles : max_pairs;
+        const int cap = std::min(max_pairs, num_sms / 2);  // a caller's SM budget caps it too
+        const int pairs = std::max(1, std::min(total_tiles, cap));
         grid = 2 * pairs;
     }
     cfg.gridDim = dim3((unsigned)grid, 1, 1);

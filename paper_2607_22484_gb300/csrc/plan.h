@@ -194,10 +194,11 @@ svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_
                     std::shared_ptr<Plan> *keep = nullptr);
 // Drop cached plans nobody else holds once the cache exceeds max_entries (under ctx->mu).
 void evict_plans(svt_ctx *ctx, size_t max_entries);
-svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s);
+// sms: SMs the product launches may use (0 = all of the device).
+svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, int sms = 0);
 // Ops [first, last) of a plan only (the serving loop advances requests op by op).
 svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, size_t first,
-                   size_t last);
+                   size_t last, int sms = 0);
 // Read the plan's internal status word back to host memory (async on s).
 svt_status plan_status_copy(svt_ctx *ctx, const Plan &P, int *host_dst, cudaStream_t s);
 void serve_shutdown(svt_ctx *ctx);

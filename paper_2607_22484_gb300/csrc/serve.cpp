@@ -30,6 +30,8 @@
 #include <array>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <list>
@@ -46,7 +48,33 @@ namespace {
 
 constexpr int kStreams = 8;
 constexpr int kSlots = 16;
+// Two lanes share the SMs. Requests of at least kLargeElems elements run as one fused
+// persistent solve each (the large lane, one at a time, at most num_sms - kSmallSms
+// SMs); smaller ones advance stage by stage in windows (the small lane), whose
+// grids shrink to kSmallSms while a large solve runs. A large solve then never
+// holds up the short windows, and large requests keep the efficient fused path.
+constexpr int64_t kLargeElems = (int64_t)8 << 20;
+constexpr int kSmallSms = 32;
 constexpr size_t kQueueLimit = 1 << 16;
+
+// Optional scheduler trace: with SVT_SERVE_TRACE=<file> in the environment, one line
+// per scheduler event (time in ms, event, ticket, detail) is appended to the file.
+FILE *trace_file()
+{
+    static FILE *f = [] {
+        const char *p = std::getenv("SVT_SERVE_TRACE");
+        return p && *p ? std::fopen(p, "a") : nullptr;
+    }();
+    return f;
+}
+
+double now_ms();
+
+void trace(const char *ev, uint64_t ticket, long long detail)
+{
+    if (FILE *f = trace_file())
+        std::fprintf(f, "%.3f %s %llu %lld\n", now_ms(), ev, (unsigned long long)ticket, detail);
+}
 
 double now_ms()
 {
@@ -113,6 +141,7 @@ struct Request {
     std::shared_ptr<Plan> plan_ref;  // keeps the plan alive while ops are in flight
     size_t pc = 0;          // next op of the plan to issue
     bool grouped = false;   // ops limited to the kinds the grouped kernels cover
+    bool large = false;     // large lane: one fused solve
 };
 
 // Device tables of one serving window live in a ring of slots at the end of the
@@ -191,7 +220,10 @@ struct ServeState {
     bool stop = false;
     bool started = false;
     uint64_t next_ticket = 1;
-    std::deque<Request *> queue;
+    std::deque<Request *> queue;   // small lane, arrival order
+    std::deque<Request *> bigq;    // large lane, arrival order
+    Request *big = nullptr;        // the large solve in flight
+    cudaStream_t big_stream = nullptr;
     std::list<Request *> active;
     std::map<uint64_t, Request *> tickets;
     Arena arena;
@@ -228,6 +260,8 @@ svt_status start_workers(svt_ctx *ctx, ServeState *s)
     if (!s->h_status && cudaMallocHost(reinterpret_cast<void **>(&s->h_status), sizeof(int) * kSlots) != cudaSuccess)
         return SVT_ERR_CUDA;
     if (!s->win && cudaStreamCreateWithFlags(&s->win, cudaStreamNonBlocking) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    if (!s->big_stream && cudaStreamCreateWithFlags(&s->big_stream, cudaStreamNonBlocking) != cudaSuccess)
         return SVT_ERR_CUDA;
     if (!s->h_ring && cudaMallocHost(reinterpret_cast<void **>(&s->h_ring), kRingBytes) != cudaSuccess)
         return SVT_ERR_CUDA;
@@ -267,7 +301,7 @@ void finish(ServeState *s, Request *r, svt_status st)
 // One serving window: grouped ingest of newly admitted requests, one grouped
 // product launch per tile width holding the next product stage of every active
 // request, grouped finalize of requests that reached their last op.
-svt_status issue_window(svt_ctx *ctx, ServeState *s)
+svt_status issue_window(svt_ctx *ctx, ServeState *s, int sms)
 {
     // Ring slot for this window's tables.
     const int k = s->ring_next;
@@ -439,7 +473,7 @@ svt_status issue_window(svt_ctx *ctx, ServeState *s)
         L.gtab = reinterpret_cast<const TcProblem *>(d + o_p[g]);
         L.gstart = reinterpret_cast<const int *>(d + o_s[g]);
         L.gcount = (int)probs[g].size();
-        if (tc_gemm_launch_grouped(L, g ? 256 : 128, tiles[g], ctx->num_sms, st) != cudaSuccess)
+        if (tc_gemm_launch_grouped(L, g ? 256 : 128, tiles[g], sms, st) != cudaSuccess)
             return SVT_ERR_CUDA;
         ++launched;
     }
@@ -452,7 +486,7 @@ svt_status issue_window(svt_ctx *ctx, ServeState *s)
         svt_status e;
         {
             std::lock_guard<std::mutex> g(ctx->mu);
-            e = run_ops(ctx, *r->plan, a, st, r->pc, last);
+            e = run_ops(ctx, *r->plan, a, st, r->pc, last, sms);
         }
         if (e != SVT_OK)
             return e;
@@ -502,11 +536,62 @@ bool tick(svt_ctx *ctx, ServeState *s)
             continue;
         }
         finish(s, r, q == cudaSuccess ? (svt_status)s->h_status[r->slot] : SVT_ERR_CUDA);
+        trace("done", r->ticket, (long long)r->result);
+        if (r == s->big)
+            s->big = nullptr;
         it = s->active.erase(it);
         progress = true;
     }
-    // Admit in arrival order while a slot and workspace are free.
-    while (!s->queue.empty() && (int)s->active.size() < kSlots) {
+    // Large lane: the oldest large request runs as one fused solve once no other one
+    // runs and its workspace fits. While it waits for workspace no new small request
+    // is admitted (the running ones free theirs within milliseconds).
+    bool hold_small = false;
+    if (!s->big && !s->bigq.empty() && (int)s->active.size() < kSlots) {
+        Request *r = s->bigq.front();
+        size_t off;
+        if (!s->arena.alloc(r->ws_len, &off)) {
+            hold_small = true;
+            trace("hold", r->ticket, (long long)r->ws_len);
+        } else {
+            s->bigq.pop_front();
+            const double t0 = trace_file() ? now_ms() : 0.0;
+            int slot = 0;
+            while (s->slot_used[slot])
+                ++slot;
+            s->slot_used[slot] = true;
+            r->slot = slot;
+            r->ws_off = off;
+            Plan *plan = nullptr;
+            svt_status e;
+            {
+                std::lock_guard<std::mutex> g(ctx->mu);
+                evict_plans(ctx, 512);
+                e = get_plan(ctx, r->m.m, r->m.n, r->opt, off, ctx->ws_bytes - kRingBytes - off,
+                             &plan, 0, &r->plan_ref);
+                if (e == SVT_OK) {
+                    CallArgs a{r->m.A, r->m.lda, r->m.tau, r->m.Y, r->m.ldy, r->m.d_status};
+                    e = run_plan(ctx, *plan, a, s->big_stream, ctx->num_sms - kSmallSms);
+                }
+                if (e == SVT_OK)
+                    e = plan_status_copy(ctx, *plan, &s->h_status[slot], s->big_stream);
+            }
+            if (e == SVT_OK && cudaEventRecord(s->events[slot], s->big_stream) != cudaSuccess)
+                e = SVT_ERR_CUDA;
+            trace("large_launch", r->ticket, trace_file() ? (long long)((now_ms() - t0) * 1e3) : 0);
+            if (e != SVT_OK) {
+                cudaStreamSynchronize(s->big_stream);
+                finish(s, r, e);
+            } else {
+                r->plan = plan;
+                r->state = 3;
+                s->active.push_back(r);
+                s->big = r;
+            }
+            progress = true;
+        }
+    }
+    // Small lane: admit in arrival order while a slot and workspace are free.
+    while (!hold_small && !s->queue.empty() && (int)s->active.size() < kSlots) {
         Request *r = s->queue.front();
         size_t off;
         if (!s->arena.alloc(r->ws_len, &off))
@@ -520,12 +605,14 @@ bool tick(svt_ctx *ctx, ServeState *s)
         r->ws_off = off;
         Plan *plan = nullptr;
         svt_status e;
+        const double t0 = trace_file() ? now_ms() : 0.0;
         {
             std::lock_guard<std::mutex> g(ctx->mu);
             evict_plans(ctx, 512);  // plans of active requests stay alive through plan_ref
             e = get_plan(ctx, r->m.m, r->m.n, r->opt, off, ctx->ws_bytes - kRingBytes - off, &plan,
                          0, &r->plan_ref);
         }
+        trace("admit", r->ticket, trace_file() ? (long long)((now_ms() - t0) * 1e3) : 0);
         if (e != SVT_OK) {
             finish(s, r, e);
             progress = true;
@@ -544,9 +631,11 @@ bool tick(svt_ctx *ctx, ServeState *s)
         if (r->state == 1)
             any = true;
     if (any) {
-        svt_status e = issue_window(ctx, s);
+        const double t0 = trace_file() ? now_ms() : 0.0;
+        svt_status e = issue_window(ctx, s, s->big ? kSmallSms : ctx->num_sms);
         if (e == SVT_ERR_NOT_READY)
             return progress;
+        trace("window", s->windows, trace_file() ? (long long)((now_ms() - t0) * 1e3) : 0);
         if (e != SVT_OK) {
             for (auto it = s->active.begin(); it != s->active.end();) {
                 Request *r = *it;
@@ -819,6 +908,10 @@ void serve_shutdown(svt_ctx *ctx)
         cudaStreamSynchronize(s->win);
         cudaStreamDestroy(s->win);
     }
+    if (s->big_stream) {
+        cudaStreamSynchronize(s->big_stream);
+        cudaStreamDestroy(s->big_stream);
+    }
     for (int i = 0; i < kRing; ++i)
         if (s->ring_ev[i])
             cudaEventDestroy(s->ring_ev[i]);
@@ -827,6 +920,7 @@ void serve_shutdown(svt_ctx *ctx)
     // Every request lives in `tickets` from submission until its release (queued and
     // active ones included), so the ticket map owns them all.
     s->queue.clear();
+    s->bigq.clear();
     s->active.clear();
     for (auto &kv : s->tickets)
         delete kv.second;
@@ -841,7 +935,7 @@ bool serve_busy(svt_ctx *ctx)
     if (!s)
         return false;
     std::lock_guard<std::mutex> g(s->mu);
-    return !s->queue.empty() || !s->active.empty();
+    return !s->queue.empty() || !s->bigq.empty() || !s->active.empty();
 }
 
 } // namespace svt
@@ -1027,9 +1121,11 @@ svt_status svt_serve_submit(svt_ctx_t ctx, const svt_matrix *req, uint64_t *tick
     Resolved r;
     if (!resolve(&req->opt, &r))
         return SVT_ERR_INVALID;
-    r.fuse = 0;  // serving windows group per-stage problems across requests
     if (r.prec == SVT_FP64 && (req->m > kF64MaxDim || req->n > kF64MaxDim))
         return SVT_ERR_UNSUPPORTED;
+    // Large requests: one fused solve; small ones: per-stage problems grouped in windows.
+    const bool large = req->m * req->n >= kLargeElems && r.prec != SVT_FP64;
+    r.fuse = large ? 1 : 0;
     size_t need = align_up(make_layout(req->m, req->n, r).total, kAlign);
     if (ctx->ws_bytes < kRingBytes || need > ctx->ws_bytes - kRingBytes)
         return SVT_ERR_OOM;
@@ -1046,7 +1142,7 @@ svt_status svt_serve_submit(svt_ctx_t ctx, const svt_matrix *req, uint64_t *tick
         s->thread = std::thread(scheduler, ctx, s);
         s->started = true;
     }
-    if (s->queue.size() >= kQueueLimit)
+    if (s->queue.size() + s->bigq.size() >= kQueueLimit)
         return SVT_ERR_BUSY;
     auto *q = new Request();
     q->ticket = s->next_ticket++;
@@ -1054,7 +1150,9 @@ svt_status svt_serve_submit(svt_ctx_t ctx, const svt_matrix *req, uint64_t *tick
     q->opt = r;
     q->ws_len = need;
     q->t_submit = now_ms();
-    s->queue.push_back(q);
+    q->large = large;
+    (large ? s->bigq : s->queue).push_back(q);
+    trace("submit", q->ticket, large ? 1 : 0);
     s->tickets[q->ticket] = q;
     *ticket = q->ticket;
     s->cv.notify_all();

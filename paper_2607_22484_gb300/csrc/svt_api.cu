@@ -681,8 +681,9 @@ __global__ void prep_kernel(const float *__restrict__ A, int64_t lda, int wide, 
 } // namespace
 
 svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, size_t first,
-                   size_t last)
+                   size_t last, int sms)
 {
+    const int grid_sms = (sms > 0 && sms < ctx->num_sms) ? sms : ctx->num_sms;
     uint8_t *base = ctx->ws + P.ws_base;
     const Layout &L = P.lay;
     double *scal = reinterpret_cast<double *>(base + L.scal);
@@ -728,7 +729,7 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
                 e1 = ctx->prof_pool[ctx->prof_next++];
                 cudaEventRecord(e0, s);
             }
-            err = tc_gemm_launch_fused(l, P.fused_bn, P.fused_tiles, ctx->num_sms, s);
+            err = tc_gemm_launch_fused(l, P.fused_bn, P.fused_tiles, grid_sms, s);
             if (ctx->profile) {
                 cudaEventRecord(e1, s);
                 ctx->prof_pending.push_back({e0, e1, P.fused_flops});
@@ -795,7 +796,7 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
                 e1 = ctx->prof_pool[ctx->prof_next++];
                 cudaEventRecord(e0, s);
             }
-            err = tc_gemm_launch(l, op.bn, ctx->num_sms, s);
+            err = tc_gemm_launch(l, op.bn, grid_sms, s);
             if (ctx->profile) {
                 cudaEventRecord(e1, s);
                 ctx->prof_pending.push_back({e0, e1, P.tc_flops[op.idx]});
@@ -849,9 +850,9 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
     return SVT_OK;
 }
 
-svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s)
+svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, int sms)
 {
-    return run_ops(ctx, P, a, s, 0, P.ops.size());
+    return run_ops(ctx, P, a, s, 0, P.ops.size(), sms);
 }
 
 namespace {

@@ -41,13 +41,17 @@ def test_batch_matches_oracle_and_single():
 
 
 def _serve(ctx, items, tiers, statuses=None):
-    tickets, outs = [], []
-    for i, it in enumerate(items):
+    # Inputs are made before the first submission: generating them in between would
+    # compete for the host cores with the serving thread.
+    outs = []
+    for it in items:
         a = torch.from_numpy(it.matrix()).cuda()
-        y = torch.full_like(a, float("nan"))
+        outs.append((a, torch.full_like(a, float("nan"))))
+    torch.cuda.synchronize()
+    tickets = []
+    for i, (it, (a, y)) in enumerate(zip(items, outs)):
         st = statuses[i] if statuses is not None else None
         tickets.append(ctx.submit(a, it.tau, y, status=st, iters=20, prec=tiers[i]))
-        outs.append((a, y))
     results = {}
     t0 = time.time()
     while len(results) < len(tickets) and time.time() - t0 < 120:
@@ -202,3 +206,50 @@ def test_destroy_with_requests_queued_and_in_flight():
     y = fresh.polar(a, it.tau, iters=20, prec="bf16")
     torch.cuda.synchronize()
     assert bool(torch.isfinite(y).all())
+
+
+def test_serving_large_lane_beside_small_requests():
+    """Requests of at least 8 Mi elements run as fused solves on the large lane while
+    small ones keep advancing in windows on the reserved SMs: every result equals the
+    same solve alone, and small requests submitted behind a long large solve finish
+    well before it."""
+    rng = np.random.default_rng(52)
+
+    class Item:
+        def __init__(self, m, n, seed):
+            self.m, self.n, self.seed = m, n, seed
+            self.tau = wl.noise_edge(m, n) + 0.5
+
+        def matrix(self):
+            return wl.low_rank_plus_noise(self.m, self.n, 20, self.seed, 2.0, 10.0)
+
+    # a long large request (8192 x 4096 in the FP32 tier) first, a shorter one later
+    items, tiers = [Item(8192, 4096, 1)], ["fp32"]
+    for k in range(10):
+        s = int(rng.choice([256, 384, 512]))
+        items.append(Item(s, s // 2 if k % 2 else s, 10 + k))
+        tiers.append("bf16" if k % 3 else "fp32")
+    items.append(Item(2048, 4096, 2))
+    tiers.append("bf16")
+    for k in range(5):
+        items.append(Item(320, 320, 30 + k))
+        tiers.append("bf16")
+    need = sum(pkg.workspace_bytes(it.m, it.n, prec=t) for it, t in zip(items, tiers))
+    ctx = pkg.Context(0, workspace_bytes=need + (64 << 20))
+    tickets, _, _ = _serve(ctx, items, tiers)  # warm-up: plans, first kernel launches
+    for t in tickets:
+        ctx.release(t)
+    tickets, outs, results = _serve(ctx, items, tiers)
+    alone = pkg.Context(0, workspace_bytes=1 << 20)
+    lat_large, lat_small = [], []
+    for it, tier, t, (a, y) in zip(items, tiers, tickets, outs):
+        stt, lat = results[t]
+        assert stt == 0, pkg.status_str(stt)
+        (lat_large if it.m * it.n >= (8 << 20) else lat_small).append(lat)
+        ref = alone.polar(a, it.tau, iters=20, prec=tier)
+        torch.cuda.synchronize()
+        assert oracle.relerr(y.cpu().numpy(), ref.cpu().numpy()) < 1e-5
+        assert ctx.release(t) == 0
+    print(f"small-request latency median {np.median(lat_small):.2f} ms, large {lat_large}")
+    # the small requests submitted behind the long solve finish well before it
+    assert np.median(lat_small) < 0.5 * lat_large[0], (np.median(lat_small), lat_large)
