@@ -262,6 +262,22 @@ __device__ bool wait_counter(const int *counter, int target, volatile int *abort
     }
 }
 
+// Wait for strip `idx` of dependency k of problem P (see TcProblem::sdep_*), unless the
+// producing problem is already known (src_done) or found to be complete as a whole,
+// which covers every strip; a role then stops checking that source.
+__device__ __forceinline__ bool wait_strip(const TcLaunch &L, const TcProblem &P, int k, int idx,
+                                           bool &src_done, volatile int *abort_flag, int *status)
+{
+    if (src_done)
+        return true;
+    if (ld_acquire_gpu(&L.done[P.sdep_src[k]]) >= P.sdep_whole[k]) {
+        src_done = true;
+        return true;
+    }
+    return wait_counter(&L.strips[P.sdep_base[k] + idx], P.sdep_target[k], abort_flag, status,
+                        kWaitTimeoutNs);
+}
+
 // Shared-memory matrix descriptor for a K-major operand tile laid out by TMA
 // with 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
@@ -402,11 +418,12 @@ __device__ __forceinline__ const TcProblem &prob_at(const TcLaunch &L, int p)
 // Linear tile index -> (problem, tile row, tile column) for tiles of TM x BN.
 // Dense problems: column-major over the tile grid. Symmetric problems: only
 // tiles holding some element with row <= col; column tn holds r (tn + 1) row
-// tiles (r = BN / TM), so the first tile of column tn is r tn (tn + 1) / 2.
+// tiles (r = BN / TM), so the first tile of column tn is r tn (tn + 1) / 2
+// (ROWMAJOR_SYM with square tiles: row-major instead, see below).
 // A role's tile indices only increase, so the problem search gallops forward from
 // the previous answer (`hint`) instead of bisecting the whole table: a few
 // dependent loads of the tile prefix sums instead of log2(problems).
-template <int BN, int TM>
+template <int BN, int TM, bool ROWMAJOR_SYM>
 __device__ TileCoord decode_tile(const TcLaunch &L, int t, int &hint)
 {
     TileCoord tc{0, 0, 0, false};
@@ -446,6 +463,24 @@ __device__ TileCoord decode_tile(const TcLaunch &L, int t, int &hint)
         return tc;
     }
     constexpr int r = BN / TM;
+    if (ROWMAJOR_SYM && r == 1) {
+        // Square tiles: row-major over the upper triangle (row tm holds columns
+        // tm .. T - 1, first index tm T - tm (tm - 1) / 2), so that the strips of a
+        // symmetric product complete in order.
+        const int T = P.tiles_n;
+        auto first = [T](int i) { return i * T - i * (i - 1) / 2; };
+        const float b = 2.0f * (float)T + 1.0f;
+        int tm = (int)((b - sqrtf(fmaxf(b * b - 8.0f * (float)local, 0.0f))) * 0.5f);
+        tm = tm < 0 ? 0 : (tm > T - 1 ? T - 1 : tm);
+        while (tm > 0 && first(tm) > local)
+            --tm;
+        while (tm + 1 < T && first(tm + 1) <= local)
+            ++tm;
+        tc.tm = tm;
+        tc.tn = tm + (local - first(tm));
+        tc.valid = (tm < P.tiles_m) && (tc.tn < P.tiles_n);
+        return tc;
+    }
     int tn = (int)((sqrtf(8.0f * (float)local / (float)r + 1.0f) - 1.0f) * 0.5f);
     while (tn > 0 && r * tn * (tn + 1) / 2 > local)
         --tn;
@@ -498,6 +533,7 @@ struct EpiHot {
     int64_t ldc, ldo, ldt;
     float alpha, beta, gamma;
     int M, N, sym, otma, ttma, c_kind, c_trans, o_kind, o_trans, t_kind;
+    int strip_base, tiles_m;  // fused solves: the problem's strip counters
 };
 
 // Raw C values of one lane's 32-column row segment: BF16 hi in q[0..3] (lo of a
@@ -883,6 +919,8 @@ __device__ __forceinline__ void load_hot(EpiHot &h, const TcProblem &P, const Ca
     h.ttma = P.t_tma;
     h.c_kind = e.c_kind;
     h.c_trans = e.c_trans;
+    h.strip_base = P.strip_base;  // read only by strip launches
+    h.tiles_m = P.tiles_m;
     h.o_kind = e.o_kind;
     h.o_trans = e.o_trans;
     h.t_kind = e.t_kind;
@@ -911,9 +949,10 @@ __device__ __forceinline__ void load_hot(EpiHot &h, const TcProblem &P, const Ca
 
 constexpr int kRingTiles = 4;  // fused launches: tile ids in flight between the roles
 
-template <int BN, int STAGES, bool CHAIN, bool PAIR, int NSTG>
+template <int BN, int STAGES, bool CHAIN, bool PAIR, int NSTG, bool STRIPS>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcLaunch L)
 {
+    static_assert(!STRIPS || CHAIN, "strip dependencies exist in fused launches only");
     static_assert(!PAIR || BN == 256, "CTA pairs compute 256 x 256 tiles");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -998,6 +1037,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         int ri = 0;
         uint32_t rphase = 0;
         int hint = 0;
+        int dep_prob = -1;       // problem whose whole dependencies have been waited for
+        bool src_done[2] = {false, false};
+        int smode[2] = {0, 0};   // that problem's strip dependencies of L and R
         for (int t = t_first; ok; t += t_step) {
             TileCoord tc;
             if (CHAIN) {
@@ -1010,7 +1052,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                     t = (t < total) ? t : -1;
                     tc = TileCoord{-1, 0, 0, false};
                     if (t >= 0)
-                        tc = decode_tile<BN, TILE_ROWS>(L, t, hint);
+                        tc = decode_tile<BN, TILE_ROWS, STRIPS>(L, t, hint);
                     const int ent[4] = {t, tc.valid ? tc.prob : -1, tc.tm, tc.tn};
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
@@ -1042,7 +1084,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             } else {
                 if (t >= total)
                     break;
-                tc = decode_tile<BN, TILE_ROWS>(L, t, hint);
+                tc = decode_tile<BN, TILE_ROWS, STRIPS>(L, t, hint);
             }
             if (!tc.valid)
                 continue;
@@ -1051,11 +1093,31 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             const int row0 = (PAIR ? 2 * tc.tm + (int)rank : tc.tm) * kBM;
             const int col0 = tc.tn * BN + (int)rank * B_ROWS;
             if (CHAIN) {
-                // Operands are results of earlier problems: wait until they are complete.
-                for (int d = 0; d < 2 && ok; ++d)
-                    if (P.dep[d] >= 0)
-                        ok = wait_counter(&L.done[P.dep[d]], P.dep_target[d], abort_flag, status0,
-                                          kWaitTimeoutNs);
+                // Operands are results of earlier problems: wait until they are complete
+                // (whole problems), or until the strips this tile reads are (L: the
+                // strip of this tile's row, R: of its column).
+                if (STRIPS) {
+                    if (tc.prob != dep_prob) {  // once per problem: counts only grow
+                        for (int d = 0; d < 2 && ok; ++d)
+                            if (P.dep[d] >= 0)
+                                ok = wait_counter(&L.done[P.dep[d]], P.dep_target[d], abort_flag,
+                                                  status0, kWaitTimeoutNs);
+                        dep_prob = tc.prob;
+                        smode[0] = P.sdep_mode[0];
+                        smode[1] = P.sdep_mode[1];
+                        src_done[0] = !smode[0];
+                        src_done[1] = !smode[1];
+                    }
+                    for (int q = 0; q < 2 && ok; ++q)
+                        if (!src_done[q])
+                            ok = wait_strip(L, P, q, q ? tc.tn : tc.tm, src_done[q], abort_flag,
+                                            status0);
+                } else {
+                    for (int d = 0; d < 2 && ok; ++d)
+                        if (P.dep[d] >= 0)
+                            ok = wait_counter(&L.done[P.dep[d]], P.dep_target[d], abort_flag,
+                                              status0, kWaitTimeoutNs);
+                }
                 fence_async_global();  // the TMA reads below come after the acquire
                 if (!ok)
                     break;
@@ -1131,7 +1193,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             } else {
                 if (t >= total)
                     break;
-                tc = decode_tile<BN, TILE_ROWS>(L, t, hint);
+                tc = decode_tile<BN, TILE_ROWS, STRIPS>(L, t, hint);
             }
             if (!tc.valid)
                 continue;
@@ -1198,6 +1260,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         int buf = 0;
         uint32_t tphase = 0;
         int last_prob = -1;
+        bool c_done = true;
         EpiHot h;
         int ri = 0;
         uint32_t rphase = 0;
@@ -1228,14 +1291,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             } else {
                 if (t >= total)
                     break;
-                tc = decode_tile<BN, TILE_ROWS>(L, t, hint);
+                tc = decode_tile<BN, TILE_ROWS, STRIPS>(L, t, hint);
             }
             if (!tc.valid)
                 continue;
-            if (PAIR)
-                tc.tm = 2 * tc.tm + (int)rank;  // this CTA's 128-row half of the tile
             const TcProblem &P = prob_at(L, tc.prob);
-            if (CHAIN && (P.ep.c_kind != C_NONE || P.ep.theta_src)) {
+            if (CHAIN && !STRIPS && (P.ep.c_kind != C_NONE || P.ep.theta_src)) {
                 // C or the norm bound is an earlier result: make it visible to these loads.
                 for (int d = 0; d < 2; ++d)
                     if (P.dep[d] >= 0 && lane == 0)
@@ -1243,6 +1304,28 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                                      kWaitTimeoutNs);
                 __syncwarp();
             }
+            if (STRIPS) {
+                // C or the norm bound is an earlier result: make it visible to these loads;
+                // earlier readers of the buffers this tile overwrites must be done.
+                if (lane == 0) {
+                    if (tc.prob != last_prob) {  // once per problem: counts only grow
+                        if (P.ep.c_kind != C_NONE || P.ep.theta_src)
+                            for (int d = 0; d < 2; ++d)
+                                if (P.dep[d] >= 0)
+                                    wait_counter(&L.done[P.dep[d]], P.dep_target[d], abort_flag,
+                                                 status0, kWaitTimeoutNs);
+                        for (int d = 0; d < P.nwdep; ++d)
+                            wait_counter(&L.done[P.wdep[d]], P.wdep_target[d], abort_flag,
+                                         status0, kWaitTimeoutNs);
+                        c_done = !P.sdep_mode[2];
+                    }
+                    if (!c_done)
+                        wait_strip(L, P, 2, tc.tm, c_done, abort_flag, status0);
+                }
+                __syncwarp();
+            }
+            if (PAIR)
+                tc.tm = 2 * tc.tm + (int)rank;  // this CTA's 128-row half of the tile
             if (tc.prob != last_prob) {
                 load_hot(h, P, calls);
                 last_prob = tc.prob;
@@ -1319,6 +1402,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                     fence_async_global();
                     __threadfence();
                     atomicAdd(&L.done[P.pid], 1);
+                    if (STRIPS && h.strip_base >= 0) {  // the strips this tile completes a part of
+                        int *sp = L.strips + h.strip_base;
+                        const int sr = PAIR ? (tc.tm >> 1) : tc.tm;  // tile (pair) row
+                        atomicAdd(sp + sr, 1);
+                        if (!h.sym)
+                            atomicAdd(sp + h.tiles_m + tc.tn, 1);
+                        else if (tc.tn != sr)
+                            atomicAdd(sp + tc.tn, 1);
+                    }
                 }
                 __syncwarp();
             }
@@ -1353,12 +1445,12 @@ constexpr int smem_bytes()
 
 // One launch of the product kernel over total_tiles tiles (tile-width code's
 // tiles: CTA pairs for kBnPair). Persistent: at most one CTA (pair) per SM (pair).
-template <int BN, int STAGES, bool CHAIN, bool PAIR, int NSTG>
+template <int BN, int STAGES, bool CHAIN, bool PAIR, int NSTG, bool STRIPS = false>
 cudaError_t launch_kernel(const TcLaunch &l, int total_tiles, int num_sms, cudaStream_t s)
 {
     constexpr int smem = smem_bytes<BN, STAGES, PAIR, NSTG>();
     static_assert(smem <= 232448, "shared memory per CTA");
-    auto kern = tc_gemm_kernel<BN, STAGES, CHAIN, PAIR, NSTG>;
+    auto kern = tc_gemm_kernel<BN, STAGES, CHAIN, PAIR, NSTG, STRIPS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess)
         return e;
@@ -1422,10 +1514,17 @@ cudaError_t tc_gemm_launch_grouped(const TcLaunch &l, int bn, int total_tiles, i
 }
 
 cudaError_t tc_gemm_launch_fused(const TcLaunch &l, int bn, int total_tiles, int num_sms,
-                                 cudaStream_t s)
+                                 cudaStream_t s, bool strips)
 {
     TcLaunch g = l;
     g.nprob = 0;
+    if (strips) {  // square tiles only: per-strip dependencies
+        if (bn == 128)
+            return launch_kernel<128, 5, true, false, 2, true>(g, total_tiles, num_sms, s);
+        if (bn == kBnPair)
+            return launch_kernel<256, 6, true, true, 1, true>(g, total_tiles, num_sms, s);
+        return cudaErrorInvalidValue;
+    }
     return launch_width<true>(g, bn, total_tiles, num_sms, s);
 }
 

@@ -51,6 +51,8 @@ struct Layout {
     int64_t M = 0, N = 0, ldM = 0, ldN = 0;
     size_t esz = 2;          // element size of matrix buffers (2 BF16, 8 FP64)
     size_t scal = 0, status = 0, counters = 0, colnorm = 0;
+    size_t strips = 0, strips_bytes = 0;  // fused solves: strip counters (at the end)
+    int max_strips = 0;                   // strip counters per problem
     int max_problems = 0;    // capacity of the fused counters / table
     size_t fused_tab = 0, fused_tab_bytes = 0;
     Buf X[2], Xt[2], XtLo0, S[2], Yp, Zp, Ys, Zs, ZPp, ZSp, B, Sp;
@@ -90,6 +92,15 @@ struct Plan {
     std::vector<PatchRec> patches;
     std::vector<double> tc_flops;   // algorithmic flops of each tensor-core launch
     std::vector<int> tc_chain;      // per problem of each launch: 0 P chain, 1 S chain, 2 both
+    // Per problem of each launch: the buffers it reads and writes (device addresses of
+    // their hi parts; null = none or the caller's), for the fused solve's dependencies.
+    struct ProbIO {
+        const void *l, *r, *c, *o, *t;
+        int o_trans;
+        const double *theta_src, *norm_acc;
+    };
+    std::vector<ProbIO> tc_io;
+    bool uses_strips = false;       // the fused launch waits on strip counters
     // Fused execution: one launch for every product (table and counters in the workspace).
     bool fused = false;
     TcLaunch fused_launch;

@@ -231,6 +231,11 @@ Layout make_layout(int64_t m, int64_t n, const Resolved &r)
         L.fused_tab_bytes = align_up(sizeof(TcProblem) * (size_t)L.max_problems, kAlign) +
                             align_up(sizeof(int) * (size_t)(L.max_problems + 1), kAlign);
         L.fused_tab = a.take(L.fused_tab_bytes);
+        // Strip counters of a fused solve, at the end so that they move no buffer: per
+        // problem at most one per 128-row tile row and 128-column tile column.
+        L.max_strips = (int)((L.M + kBM - 1) / kBM + (L.N + kBM - 1) / kBM);
+        L.strips_bytes = sizeof(int) * (size_t)L.max_problems * (size_t)L.max_strips;
+        L.strips = a.take(L.strips_bytes);
     }
     L.total = a.off;
     return L;
@@ -312,6 +317,7 @@ struct Builder {
         p.N = N;
         p.K = K;
         p.sym = sym ? 1 : 0;
+        p.strip_base = -1;
         p.tiles_m = (M + tile_rows(bn) - 1) / tile_rows(bn);
         p.tiles_n = (N + tile_cols(bn) - 1) / tile_cols(bn);
         p.ep = e;
@@ -380,6 +386,10 @@ struct Builder {
             if (!tc_problem(l.p[i], *q.L, *q.R, q.M, q.N, q.K, q.sym, q.e, bn))
                 return false;
             plan->tc_chain.push_back(q.chain);
+            plan->tc_io.push_back({ptr(q.L->hi), ptr(q.R->hi),
+                                   (q.patch & PT_C_IS_A) ? nullptr : q.e.c0,
+                                   (q.patch & PT_O_IS_Y) ? nullptr : q.e.o0, q.e.t0,
+                                   q.e.o_trans, q.e.theta_src, q.e.norm_acc});
             l.tile_start[i] = start;
             start += tc_num_tiles(l.p[i], bn);
             if (q.patch)
@@ -729,7 +739,7 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
                 e1 = ctx->prof_pool[ctx->prof_next++];
                 cudaEventRecord(e0, s);
             }
-            err = tc_gemm_launch_fused(l, P.fused_bn, P.fused_tiles, grid_sms, s);
+            err = tc_gemm_launch_fused(l, P.fused_bn, P.fused_tiles, grid_sms, s, P.uses_strips);
             if (ctx->profile) {
                 cudaEventRecord(e1, s);
                 ctx->prof_pending.push_back({e0, e1, P.fused_flops});
@@ -743,8 +753,10 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
             ++launched;
         switch (op.kind) {
         case OP_MEMSET:
-            // scalars, status and Gram diagonal are contiguous from L.scal
+            // scalars, status, counters and Gram diagonal are contiguous from L.scal
             err = cudaMemsetAsync(base + L.scal, 0, L.colnorm + (size_t)L.N * sizeof(double) - L.scal, s);
+            if (err == cudaSuccess && P.fused && P.uses_strips)
+                err = cudaMemsetAsync(base + L.strips, 0, L.strips_bytes, s);
             break;
         case OP_REDUCE:
             err = ingest_reduce_launch(a.A, P.m, P.n, a.lda, P.wide ? 1 : 0, colnorm, scal, status, s);
@@ -881,20 +893,48 @@ svt_status build_fused(svt_ctx *ctx, Plan &P)
     for (size_t i = first; i <= last; ++i)
         if (P.ops[i].kind != OP_TC)
             return SVT_OK;
+    // Dependencies. With strips (below), from the buffers each problem reads and
+    // writes: a tile waits only for the strips of the earlier results it reads (the
+    // rows of its L and R operands and its C block). Otherwise each problem waits for the whole previous
+    // problem of its chain (P or S; the combine for both), which orders every read and
+    // write of the solve at the cost of one check per problem. Before its stores, a tile
+    // waits for every earlier reader and writer of the buffers it overwrites, and for
+    // the problems that accumulate the norms it scales by.
     std::vector<TcProblem> probs;
     std::vector<int> starts, valid;
+    struct Writer {
+        int pid, mode;  // mode: 1 row-major output, 2 transposed output, 3 symmetric
+    };
+    std::map<const void *, Writer> writers;
+    std::map<const void *, std::vector<int>> readers;
+    std::map<const double *, int> norm_writer;
+    // Strips pay on CTA-pair tiles where products are 10 to 15 tiles wide (the smaller
+    // side from 2560 to under 4096: 8 % at 3072^2). On narrower products a tile's MMAs
+    // take about as long as the extra acquire loads in front of its operand copies; on
+    // wider ones the chains rarely wait for each other.
+    const int64_t tiles_wide = std::min(P.lay.M, P.lay.N) / tile_cols(bn);
+    const bool strips_ok = bn == kBnPair && tiles_wide >= 10 && tiles_wide < 16;
+    const int per_tile = kEpiWarpsPublic * ctas_per_tile(bn);
+    int strip_next = 0;
     int lastp[2] = {-1, -1};
     size_t ci = 0;
     int total = 0;
-    for (size_t i = first; i <= last; ++i) {
+    bool ok = true;
+    for (size_t i = first; i <= last && ok; ++i) {
         const int li = P.ops[i].idx;
         const TcLaunch &l = P.tc[li];
-        for (int q = 0; q < l.nprob; ++q) {
+        for (int q = 0; q < l.nprob && ok; ++q) {
             TcProblem tp = l.p[q];
+            const Plan::ProbIO io = P.tc_io[ci];
             const int chain = P.tc_chain[ci++];
-            tp.pid = (int)probs.size();
+            const int pid = (int)probs.size();
+            tp.pid = pid;
             tp.dep[0] = tp.dep[1] = -1;
             tp.dep_target[0] = tp.dep_target[1] = 0;
+            tp.nwdep = 0;
+            for (int k = 0; k < 3; ++k)
+                tp.sdep_mode[k] = tp.sdep_base[k] = tp.sdep_target[k] = tp.sdep_src[k] =
+                    tp.sdep_whole[k] = 0;
             tp.patch = 0;
             tp.call_idx = 0;
             for (const PatchRec &pr : P.patches)
@@ -902,25 +942,123 @@ svt_status build_fused(svt_ctx *ctx, Plan &P)
                     tp.patch |= pr.flags;
             if (tp.patch & PT_O_IS_Y)
                 tp.o_tma = 0;  // the caller's output: plain coalesced stores
-            if (chain < 2) {
-                tp.dep[0] = lastp[chain];
-            } else {
-                tp.dep[0] = lastp[0];
-                tp.dep[1] = lastp[1];
+            tp.strip_base = -1;
+            if (strips_ok) {
+                tp.strip_base = strip_next;
+                strip_next += tp.sym ? tp.tiles_n : tp.tiles_m + tp.tiles_n;
+                if (tp.strip_base + (tp.sym ? tp.tiles_n : tp.tiles_m + tp.tiles_n) >
+                    P.lay.max_problems * P.lay.max_strips)
+                    ok = false;
             }
-            for (int d = 0; d < 2; ++d)
-                if (tp.dep[d] >= 0)
-                    tp.dep_target[d] = kEpiWarpsPublic * valid[tp.dep[d]];
+            auto whole = [&](int w) {
+                if (w < 0 || tp.dep[0] == w || tp.dep[1] == w)
+                    return;
+                if (tp.dep[0] < 0)
+                    tp.dep[0] = w;
+                else if (tp.dep[1] < 0)
+                    tp.dep[1] = w;
+                else
+                    ok = false;
+            };
+            auto before_store = [&](int w) {
+                if (w < 0 || w == pid)
+                    return;
+                for (int k = 0; k < tp.nwdep; ++k)
+                    if (tp.wdep[k] == w)
+                        return;
+                if (tp.nwdep < 4)
+                    tp.wdep[tp.nwdep++] = w;
+                else
+                    ok = false;
+            };
+            if (!strips_ok) {
+                if (chain < 2) {
+                    tp.dep[0] = lastp[chain];
+                } else {
+                    tp.dep[0] = lastp[0];
+                    tp.dep[1] = lastp[1];
+                }
+                for (int k = 0; k < 2; ++k)
+                    if (tp.dep[k] >= 0)
+                        tp.dep_target[k] = kEpiWarpsPublic * valid[tp.dep[k]];
+                if (chain < 2)
+                    lastp[chain] = pid;
+                else
+                    lastp[0] = lastp[1] = pid;
+                starts.push_back(total);
+                total += tc_num_tiles(tp, bn);
+                valid.push_back(tc_valid_ctas(tp, bn));
+                probs.push_back(tp);
+                continue;
+            }
+            // RAW: L, R (producer) and C (epilogue)
+            const void *in[3] = {io.l, io.r, io.c};
+            for (int k = 0; k < 3; ++k) {
+                if (!in[k])
+                    continue;
+                auto it = writers.find(in[k]);
+                if (it == writers.end())
+                    continue;  // written before this launch
+                const Writer w = it->second;
+                const TcProblem &src = probs[w.pid];
+                if (strips_ok) {
+                    tp.sdep_mode[k] = w.mode;
+                    tp.sdep_base[k] = src.strip_base + (w.mode == 2 ? src.tiles_m : 0);
+                    tp.sdep_target[k] =
+                        per_tile * (w.mode == 2 ? src.tiles_m : src.tiles_n);
+                    tp.sdep_src[k] = w.pid;
+                    tp.sdep_whole[k] = kEpiWarpsPublic * valid[w.pid];
+                } else {
+                    whole(w.pid);
+                }
+            }
+            // norms this problem's scales are computed from
+            if (io.theta_src) {
+                auto it = norm_writer.find(io.theta_src);
+                if (it != norm_writer.end())
+                    before_store(it->second);
+            }
+            // WAR / WAW on the buffers this problem writes
+            const void *outs[2] = {io.o, io.t};
+            for (const void *b : outs) {
+                if (!b)
+                    continue;
+                auto rd = readers.find(b);
+                if (rd != readers.end())
+                    for (int r : rd->second)
+                        before_store(r);
+                auto wr = writers.find(b);
+                if (wr != writers.end())
+                    before_store(wr->second.pid);
+            }
+            for (int k = 0; k < 2; ++k)
+                if (tp.dep[k] >= 0)
+                    tp.dep_target[k] = kEpiWarpsPublic * valid[tp.dep[k]];
+            for (int k = 0; k < tp.nwdep; ++k)
+                tp.wdep_target[k] = kEpiWarpsPublic * valid[tp.wdep[k]];
+            // record this problem's reads and writes
+            for (int k = 0; k < 3; ++k)
+                if (in[k])
+                    readers[in[k]].push_back(pid);
+            if (io.o) {
+                writers[io.o] = {pid, tp.sym ? 3 : (io.o_trans ? 2 : 1)};
+                readers[io.o].clear();
+            }
+            if (io.t) {
+                writers[io.t] = {pid, 2};
+                readers[io.t].clear();
+            }
+            if (io.norm_acc)
+                norm_writer[io.norm_acc] = pid;
             starts.push_back(total);
             total += tc_num_tiles(tp, bn);
             valid.push_back(tc_valid_ctas(tp, bn));
-            if (chain < 2)
-                lastp[chain] = tp.pid;
-            else
-                lastp[0] = lastp[1] = tp.pid;
             probs.push_back(tp);
         }
     }
+    if (!ok)
+        return SVT_OK;  // not representable: the plan runs launch by launch
+    P.uses_strips = strips_ok;
     starts.push_back(total);
     if ((int)probs.size() > P.lay.max_problems)
         return SVT_OK;
@@ -942,6 +1080,7 @@ svt_status build_fused(svt_ctx *ctx, Plan &P)
     int *counters = reinterpret_cast<int *>(base + P.lay.counters);
     P.fused_launch.done = counters;
     P.fused_launch.tile_counter = counters + P.lay.max_problems;
+    P.fused_launch.strips = reinterpret_cast<int *>(base + P.lay.strips);
     P.fused_tiles = total;
     P.fused_bn = bn;
     P.fused_flops = 0.0;
@@ -1399,6 +1538,7 @@ svt_status svt_debug_gemm_bf16_ex(svt_ctx_t ctx, int nseg, const void *L_hi, con
     p.N = (int)N;
     p.K = (int)K;
     p.sym = sym ? 1 : 0;
+    p.strip_base = -1;
     p.tiles_m = (int)((M + tile_rows(bn) - 1) / tile_rows(bn));
     p.tiles_n = (int)((N + tile_cols(bn) - 1) / tile_cols(bn));
     std::memset(&p.ep, 0, sizeof(p.ep));

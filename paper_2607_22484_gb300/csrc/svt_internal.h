@@ -98,6 +98,19 @@ struct TcProblem {
     int pid;
     int dep[2];
     int dep_target[2];
+    // Finer dependencies of a fused solve (tiles with TM == BN, one strip per tile
+    // row or column): sdep[0] / [1] / [2] for the L, R and C operands, the producing
+    // problem's strip counters at sdep_base, strip index = this tile's row (L, C) or
+    // column (R), complete at sdep_target. sdep_mode: 0 none, 1 row strip of a
+    // row-major output, 2 column strip (the producer's transposed output), 3 strip of
+    // a symmetric product (its rows and columns). wdep: whole problems the epilogue
+    // waits for before its stores (earlier readers of the buffers it overwrites, the
+    // problems that accumulate the norms it scales by).
+    int sdep_mode[3], sdep_base[3], sdep_target[3];
+    int sdep_src[3], sdep_whole[3];  // producing problem and its whole-completion count
+    int strip_base;  // this problem's strip counters (-1: none): rows then columns
+    int nwdep;
+    int wdep[4], wdep_target[4];
     int nseg;
     int segL[3], segR[3];
     int M, N, K;
@@ -120,6 +133,7 @@ struct TcLaunch {
     // (tile, epilogue warp) pairs. Both live in the solve's zeroed scratch.
     int *tile_counter;
     int *done;
+    int *strips;  // fused solves: per-problem strip completion counters
     CallRec call_inline;             // per-call fields when calls == nullptr
 };
 
@@ -149,8 +163,9 @@ cudaError_t tc_gemm_launch_grouped(const TcLaunch &l, int bn, int total_tiles, i
                                    cudaStream_t s);
 // Fused launch: l.gtab / l.gstart / l.gcount hold every product of a solve in
 // dependency order; l.tile_counter and l.done point to zeroed device counters.
+// strips: the table carries per-strip dependencies (square tiles: bn 128 or kBnPair).
 cudaError_t tc_gemm_launch_fused(const TcLaunch &l, int bn, int total_tiles, int num_sms,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool strips = false);
 constexpr int kEpiWarpsPublic = 8;  // completion count per tile of a fused launch
 cudaError_t f64_gemm_launch(const F64Launch &l, cudaStream_t s);
 
