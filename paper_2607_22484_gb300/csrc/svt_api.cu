@@ -29,6 +29,7 @@
 #include <tuple>
 #include <vector>
 
+#include "fused_deps.h"
 #include "plan.h"
 
 namespace svt {
@@ -893,48 +894,26 @@ svt_status build_fused(svt_ctx *ctx, Plan &P)
     for (size_t i = first; i <= last; ++i)
         if (P.ops[i].kind != OP_TC)
             return SVT_OK;
-    // Dependencies. With strips (below), from the buffers each problem reads and
-    // writes: a tile waits only for the strips of the earlier results it reads (the
-    // rows of its L and R operands and its C block). Otherwise each problem waits for the whole previous
-    // problem of its chain (P or S; the combine for both), which orders every read and
-    // write of the solve at the cost of one check per problem. Before its stores, a tile
-    // waits for every earlier reader and writer of the buffers it overwrites, and for
-    // the problems that accumulate the norms it scales by.
-    std::vector<TcProblem> probs;
-    std::vector<int> starts, valid;
-    struct Writer {
-        int pid, mode;  // mode: 1 row-major output, 2 transposed output, 3 symmetric
-    };
-    std::map<const void *, Writer> writers;
-    std::map<const void *, std::vector<int>> readers;
-    std::map<const double *, int> norm_writer;
+    // Dependencies (fused_deps.h): whole previous problem of the chain, or per strip.
     // Strips pay on CTA-pair tiles where products are 10 to 15 tiles wide (the smaller
     // side from 2560 to under 4096: 8 % at 3072^2). On narrower products a tile's MMAs
     // take about as long as the extra acquire loads in front of its operand copies; on
     // wider ones the chains rarely wait for each other.
     const int64_t tiles_wide = std::min(P.lay.M, P.lay.N) / tile_cols(bn);
     const bool strips_ok = bn == kBnPair && tiles_wide >= 10 && tiles_wide < 16;
-    const int per_tile = kEpiWarpsPublic * ctas_per_tile(bn);
-    int strip_next = 0;
-    int lastp[2] = {-1, -1};
+    std::vector<TcProblem> probs;
+    std::vector<DepProduct> dps;
+    std::vector<int> starts;
     size_t ci = 0;
     int total = 0;
-    bool ok = true;
-    for (size_t i = first; i <= last && ok; ++i) {
+    for (size_t i = first; i <= last; ++i) {
         const int li = P.ops[i].idx;
         const TcLaunch &l = P.tc[li];
-        for (int q = 0; q < l.nprob && ok; ++q) {
+        for (int q = 0; q < l.nprob; ++q) {
             TcProblem tp = l.p[q];
             const Plan::ProbIO io = P.tc_io[ci];
             const int chain = P.tc_chain[ci++];
-            const int pid = (int)probs.size();
-            tp.pid = pid;
-            tp.dep[0] = tp.dep[1] = -1;
-            tp.dep_target[0] = tp.dep_target[1] = 0;
-            tp.nwdep = 0;
-            for (int k = 0; k < 3; ++k)
-                tp.sdep_mode[k] = tp.sdep_base[k] = tp.sdep_target[k] = tp.sdep_src[k] =
-                    tp.sdep_whole[k] = 0;
+            tp.pid = (int)probs.size();
             tp.patch = 0;
             tp.call_idx = 0;
             for (const PatchRec &pr : P.patches)
@@ -942,122 +921,38 @@ svt_status build_fused(svt_ctx *ctx, Plan &P)
                     tp.patch |= pr.flags;
             if (tp.patch & PT_O_IS_Y)
                 tp.o_tma = 0;  // the caller's output: plain coalesced stores
-            tp.strip_base = -1;
-            if (strips_ok) {
-                tp.strip_base = strip_next;
-                strip_next += tp.sym ? tp.tiles_n : tp.tiles_m + tp.tiles_n;
-                if (tp.strip_base + (tp.sym ? tp.tiles_n : tp.tiles_m + tp.tiles_n) >
-                    P.lay.max_problems * P.lay.max_strips)
-                    ok = false;
-            }
-            auto whole = [&](int w) {
-                if (w < 0 || tp.dep[0] == w || tp.dep[1] == w)
-                    return;
-                if (tp.dep[0] < 0)
-                    tp.dep[0] = w;
-                else if (tp.dep[1] < 0)
-                    tp.dep[1] = w;
-                else
-                    ok = false;
-            };
-            auto before_store = [&](int w) {
-                if (w < 0 || w == pid)
-                    return;
-                for (int k = 0; k < tp.nwdep; ++k)
-                    if (tp.wdep[k] == w)
-                        return;
-                if (tp.nwdep < 4)
-                    tp.wdep[tp.nwdep++] = w;
-                else
-                    ok = false;
-            };
-            if (!strips_ok) {
-                if (chain < 2) {
-                    tp.dep[0] = lastp[chain];
-                } else {
-                    tp.dep[0] = lastp[0];
-                    tp.dep[1] = lastp[1];
-                }
-                for (int k = 0; k < 2; ++k)
-                    if (tp.dep[k] >= 0)
-                        tp.dep_target[k] = kEpiWarpsPublic * valid[tp.dep[k]];
-                if (chain < 2)
-                    lastp[chain] = pid;
-                else
-                    lastp[0] = lastp[1] = pid;
-                starts.push_back(total);
-                total += tc_num_tiles(tp, bn);
-                valid.push_back(tc_valid_ctas(tp, bn));
-                probs.push_back(tp);
-                continue;
-            }
-            // RAW: L, R (producer) and C (epilogue)
-            const void *in[3] = {io.l, io.r, io.c};
-            for (int k = 0; k < 3; ++k) {
-                if (!in[k])
-                    continue;
-                auto it = writers.find(in[k]);
-                if (it == writers.end())
-                    continue;  // written before this launch
-                const Writer w = it->second;
-                const TcProblem &src = probs[w.pid];
-                if (strips_ok) {
-                    tp.sdep_mode[k] = w.mode;
-                    tp.sdep_base[k] = src.strip_base + (w.mode == 2 ? src.tiles_m : 0);
-                    tp.sdep_target[k] =
-                        per_tile * (w.mode == 2 ? src.tiles_m : src.tiles_n);
-                    tp.sdep_src[k] = w.pid;
-                    tp.sdep_whole[k] = kEpiWarpsPublic * valid[w.pid];
-                } else {
-                    whole(w.pid);
-                }
-            }
-            // norms this problem's scales are computed from
-            if (io.theta_src) {
-                auto it = norm_writer.find(io.theta_src);
-                if (it != norm_writer.end())
-                    before_store(it->second);
-            }
-            // WAR / WAW on the buffers this problem writes
-            const void *outs[2] = {io.o, io.t};
-            for (const void *b : outs) {
-                if (!b)
-                    continue;
-                auto rd = readers.find(b);
-                if (rd != readers.end())
-                    for (int r : rd->second)
-                        before_store(r);
-                auto wr = writers.find(b);
-                if (wr != writers.end())
-                    before_store(wr->second.pid);
-            }
-            for (int k = 0; k < 2; ++k)
-                if (tp.dep[k] >= 0)
-                    tp.dep_target[k] = kEpiWarpsPublic * valid[tp.dep[k]];
-            for (int k = 0; k < tp.nwdep; ++k)
-                tp.wdep_target[k] = kEpiWarpsPublic * valid[tp.wdep[k]];
-            // record this problem's reads and writes
-            for (int k = 0; k < 3; ++k)
-                if (in[k])
-                    readers[in[k]].push_back(pid);
-            if (io.o) {
-                writers[io.o] = {pid, tp.sym ? 3 : (io.o_trans ? 2 : 1)};
-                readers[io.o].clear();
-            }
-            if (io.t) {
-                writers[io.t] = {pid, 2};
-                readers[io.t].clear();
-            }
-            if (io.norm_acc)
-                norm_writer[io.norm_acc] = pid;
+            dps.push_back({io.l, io.r, io.c, io.o, io.t, io.o_trans, tp.sym, chain, tp.tiles_m,
+                           tp.tiles_n, tc_valid_ctas(tp, bn), io.theta_src, io.norm_acc});
             starts.push_back(total);
             total += tc_num_tiles(tp, bn);
-            valid.push_back(tc_valid_ctas(tp, bn));
             probs.push_back(tp);
         }
     }
-    if (!ok)
+    std::vector<DepResult> deps;
+    if (!derive_fused_deps(dps, strips_ok, kEpiWarpsPublic, kEpiWarpsPublic * ctas_per_tile(bn),
+                           P.lay.max_problems * P.lay.max_strips, deps))
         return SVT_OK;  // not representable: the plan runs launch by launch
+    for (size_t k = 0; k < probs.size(); ++k) {
+        TcProblem &tp = probs[k];
+        const DepResult &d = deps[k];
+        for (int j = 0; j < 2; ++j) {
+            tp.dep[j] = d.dep[j];
+            tp.dep_target[j] = d.dep_target[j];
+        }
+        tp.nwdep = d.nwdep;
+        for (int j = 0; j < 4; ++j) {
+            tp.wdep[j] = d.wdep[j];
+            tp.wdep_target[j] = d.wdep_target[j];
+        }
+        for (int j = 0; j < 3; ++j) {
+            tp.sdep_mode[j] = d.sdep_mode[j];
+            tp.sdep_base[j] = d.sdep_base[j];
+            tp.sdep_target[j] = d.sdep_target[j];
+            tp.sdep_src[j] = d.sdep_src[j];
+            tp.sdep_whole[j] = d.sdep_whole[j];
+        }
+        tp.strip_base = d.strip_base;
+    }
     P.uses_strips = strips_ok;
     starts.push_back(total);
     if ((int)probs.size() > P.lay.max_problems)
