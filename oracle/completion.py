@@ -66,3 +66,56 @@ def kkt_residuals(x: np.ndarray, m: np.ndarray, mask: np.ndarray, lam: float):
     nuc = float(np.sum(sx))
     inner = float(np.sum(g * x))
     return float(sg.max()) / lam - 1.0, abs(inner - lam * nuc) / max(lam * nuc, 1e-300)
+
+
+def complete_continuation(m: np.ndarray, mask: np.ndarray, lam: float, lam0: float,
+                          eta: float, tol: float, max_steps: int, stage_steps: int = 0,
+                          step: float = 1.0, x0: np.ndarray | None = None):
+    """Proximal gradient with lambda continuation and a stopping test on the iterates.
+
+    Stage k (k = 0, 1, ...) solves at lambda_k = max(lam, lam0 eta^k); the stage whose
+    lambda_k equals lam is the last. Each stage runs proximal-gradient steps until the
+    relative change rho = ||X_new - X_old||_F / ||X_new||_F (0 when both are zero,
+    infinity when only X_new is zero) is <= tol, or until it has run stage_steps steps
+    (non-final stages only; 0 = no cap). The run ends when the last stage stops or after
+    max_steps steps in total.
+
+    At a fixed lambda the step map is non-expansive, so ||X_new - X_old||_F never grows
+    within a stage, and a small change bounds the optimality residual of X_new (see the
+    tests). Returns (X, info) with info = {"steps", "stages", "rel_change" (of the last
+    step), "lambdas", "changes" (||X_new - X_old||_F), "rhos" (the relative changes) and
+    "stage_of_step", each per step}.
+    """
+    if lam0 < lam:
+        raise ValueError("lam0 must be >= lam")
+    if lam0 > lam and not (0.0 < eta < 1.0):
+        raise ValueError("eta must lie in (0, 1) when lam0 > lam")
+    m = np.asarray(m, dtype=np.float64)
+    x = np.zeros_like(m) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
+    info = {"steps": 0, "stages": 0, "rel_change": 0.0, "lambdas": [], "changes": [],
+            "rhos": [], "stage_of_step": []}
+    k = 0
+    while info["steps"] < max_steps:
+        lam_k = max(lam, lam0 * eta ** k) if lam0 > lam else lam
+        last = lam_k == lam
+        info["stages"] += 1
+        taken = 0
+        while info["steps"] < max_steps:
+            x_new = prox_grad_step(x, m, mask, lam_k, step)
+            d = float(np.linalg.norm(x_new - x))
+            nx = float(np.linalg.norm(x_new))
+            rho = d / nx if nx > 0 else (0.0 if d == 0 else np.inf)
+            x = x_new
+            taken += 1
+            info["steps"] += 1
+            info["rel_change"] = rho
+            info["lambdas"].append(lam_k)
+            info["changes"].append(d)
+            info["rhos"].append(rho)
+            info["stage_of_step"].append(k)
+            if rho <= tol or (not last and stage_steps > 0 and taken >= stage_steps):
+                break
+        if last:
+            break
+        k += 1
+    return x, info

@@ -82,3 +82,101 @@ def test_limit_is_a_minimum_under_random_perturbations():
     for scale in (1e-1, 1e-2, 1e-3):
         for _ in range(300):
             assert oc.objective(x + scale * rng.standard_normal(x.shape), m, mask, lam) >= f - 1e-10
+
+
+# --- lambda continuation with a stopping test (complete_continuation)
+#
+# Pins from the mathematics of proximal gradient at a fixed lambda:
+# * the step map T is non-expansive (a gradient step of a 1-smooth convex function with
+#   h in (0, 1], then a proximal operator), so ||X_{t+1} - X_t|| = ||T X_t - T X_{t-1}||
+#   never exceeds ||X_t - X_{t-1}||: the changes do not grow within a stage;
+# * with D = X_t - X_{t+1} and r = ||D||_F, prox optimality puts (Z_t - X_{t+1}) / h in
+#   lambda d||X_{t+1}||_*, and G = P_Omega(M - X_{t+1}) differs from it by
+#   P_Omega(D) - D / h, so ||G||_2 <= lambda + (1 + 1/h) r and
+#   |<G, X_{t+1}> - lambda ||X_{t+1}||_*| <= (1 + 1/h) r ||X_{t+1}||_*. A last stage at the
+#   wrong lambda, or a wrong sign in the gradient step, breaks these bounds.
+
+def _cont_instance(seed=11):
+    m, mask = _instance(14, 11, 2, 0.6, seed)
+    s0 = np.linalg.norm(m * mask, 2)
+    return m, mask, 0.04 * s0, 0.8 * s0
+
+
+def test_continuation_changes_do_not_grow_within_a_stage():
+    m, mask, lam, lam0 = _cont_instance()
+    for step in (1.0, 0.5):
+        _, info = oc.complete_continuation(m, mask, lam, lam0, 0.5, 1e-9, 3000, step=step)
+        ch, st = info["changes"], info["stage_of_step"]
+        for i in range(1, len(ch)):
+            if st[i] == st[i - 1]:
+                assert ch[i] <= ch[i - 1] * (1 + 1e-9) + 1e-13, (i, ch[i], ch[i - 1])
+
+
+@pytest.mark.parametrize("step", [1.0, 0.5])
+def test_continuation_residual_bounds_at_the_stop(step):
+    m, mask, lam, lam0 = _cont_instance(12)
+    x, info = oc.complete_continuation(m, mask, lam, lam0, 0.5, 1e-7, 5000, step=step)
+    assert info["lambdas"][-1] == lam
+    r = info["changes"][-1]
+    g = np.where(mask != 0, m - x, 0.0)
+    sg = np.linalg.svd(g, compute_uv=False)
+    sx = np.linalg.svd(x, compute_uv=False)
+    slack = (1 + 1 / step) * r
+    assert sg[0] <= lam + slack + 1e-12, (sg[0], lam, slack)
+    assert abs(np.sum(g * x) - lam * sx.sum()) <= slack * sx.sum() + 1e-12
+    # the bound is not vacuous: the residual is close to lambda at the minimiser
+    assert sg[0] >= lam - slack - 1e-9
+
+
+@pytest.mark.parametrize("tol", [1e-5, 0.05])
+def test_continuation_stops_at_the_first_crossing(tol):
+    """Every stage ends at the first step whose relative change is <= tol; with the
+    loose tolerance some stages end after their first step."""
+    m, mask, lam, lam0 = _cont_instance(13)
+    _, info = oc.complete_continuation(m, mask, lam, lam0, 0.5, tol, 4000)
+    rho, st = np.array(info["rhos"]), np.array(info["stage_of_step"])
+    lengths = []
+    for k in np.unique(st):
+        r = rho[st == k]
+        assert r[-1] <= tol
+        assert np.all(r[:-1] > tol)
+        lengths.append(len(r))
+    if tol > 0.01:
+        assert min(lengths) == 1, lengths
+
+
+def test_continuation_stage_lambdas_and_caps():
+    m, mask, lam, lam0 = _cont_instance(14)
+    eta, cap = 0.5, 3
+    _, info = oc.complete_continuation(m, mask, lam, lam0, eta, 0.0, 40, stage_steps=cap)
+    lams, st = np.array(info["lambdas"]), np.array(info["stage_of_step"])
+    stages = int(np.ceil(np.log(lam / lam0) / np.log(eta))) + 1
+    assert info["stages"] == stages
+    for k in range(stages):
+        assert np.all(lams[st == k] == max(lam, lam0 * eta ** k))
+        if k < stages - 1:
+            assert np.sum(st == k) == cap
+    assert info["steps"] == 40 and np.sum(st == stages - 1) == 40 - cap * (stages - 1)
+
+
+def test_continuation_reaches_the_cold_start_minimum():
+    m, mask, lam, lam0 = _cont_instance(15)
+    xc, info = oc.complete_continuation(m, mask, lam, lam0, 0.5, 1e-10, 6000)
+    xs = oc.complete(m, mask, lam, 6000)
+    fc, fs = oc.objective(xc, m, mask, lam), oc.objective(xs, m, mask, lam)
+    assert abs(fc - fs) <= 1e-8 * fs, (fc, fs)
+
+
+def test_continuation_degenerate_cases():
+    m, mask, lam, lam0 = _cont_instance(16)
+    x0 = np.random.default_rng(0).standard_normal(m.shape)
+    x, info = oc.complete_continuation(m, mask, lam, lam0, 0.5, 1e-6, 0, x0=x0)
+    assert info["steps"] == 0 and info["stages"] == 0 and np.array_equal(x, x0)
+    # lam0 == lam: a single stage, the plain loop
+    x1, info1 = oc.complete_continuation(m, mask, lam, lam, 1.0, 0.0, 7)
+    assert info1["stages"] == 1 and info1["steps"] == 7
+    assert np.max(np.abs(x1 - oc.complete(m, mask, lam, 7))) == 0.0
+    with pytest.raises(ValueError):
+        oc.complete_continuation(m, mask, lam, 0.5 * lam, 0.5, 0.0, 3)
+    with pytest.raises(ValueError):
+        oc.complete_continuation(m, mask, lam, lam0, 1.0, 0.0, 3)
