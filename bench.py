@@ -300,9 +300,38 @@ def completion_extra(ctx_cls, pkg, torch, dev, steps=100, svd_steps=10):
     e1.record()
     torch.cuda.synchronize()
     ms_svd = e0.elapsed_time(e1)
+    # The same loop as one device-resident run (svt_complete: a CUDA graph with a
+    # conditional WHILE node per continuation stage): first the fixed `steps` steps,
+    # then continuation from lambda0 = 25 lambda by halves, at most 10 steps per
+    # stage before the last, stopping once ||X_new - X_old||_F / ||P_Omega(M)||_F <= tol
+    # or after `steps` steps. Each configuration runs once untimed (recording its
+    # graph) and once timed (the cached graph, relaunched from X = 0).
+    rec_host = rec(X)
+    Zd, Pd = torch.empty_like(M), torch.empty_like(M)
+    st = torch.zeros(pkg.binding.COMPLETION_STATS_BYTES, dtype=torch.uint8, device=dev)
+    device_loop = {}
+    for name, kw in (("fixed", {}),
+                     ("continuation", {"lam0": 25.0 * lam, "eta": 0.5, "tol": 1e-3,
+                                       "stage_steps": 10})):
+        for timed in (False, True):
+            X.zero_()
+            torch.cuda.synchronize()
+            e0.record()
+            ctx.complete_on_device(M, W, lam, steps, X=X, Z=Zd, Xprev=Pd, stats=st, **kw,
+                                   **opts)
+            e1.record()
+            torch.cuda.synchronize()
+        info = pkg.read_completion_stats(st)
+        device_loop[name] = {"steps": info["steps"], "stages": info["stages"],
+                             "last_rel_change": info["rel_change"], "status": info["status"],
+                             "ms": e0.elapsed_time(e1),
+                             "ms_per_step": e0.elapsed_time(e1) / max(1, info["steps"]),
+                             "recovery": rec(X), **{k: v for k, v in kw.items() if k != "lam0"}}
+    device_loop["continuation"]["lambda0_over_lambda"] = 25.0
     return {"workload": "matrix completion 4096x4096, rank 20, Bernoulli(0.2) mask, "
                         "lambda = 0.02 ||P_Omega(M)||_2, proximal gradient with step 1",
-            "steps": steps, "ms_per_step": ms / steps, "recovery": rec(X),
+            "steps": steps, "ms_per_step": ms / steps, "recovery": rec_host,
+            "device_loop": device_loop,
             "recovery_at_svd_steps": rec_at,
             "torch_svd_loop": {"steps": svd_steps, "ms_per_step": ms_svd / svd_steps,
                                "recovery": rec(Xs)},

@@ -289,6 +289,71 @@ svt_status svt_prox_grad_step(svt_ctx_t ctx, float *X, int64_t ldx, const float 
                               int64_t n, float step, float lambda, const svt_options *opt,
                               svt_status *d_status, void *stream);
 
+/*
+ * svt_complete: proximal-gradient matrix completion (the problem of
+ * svt_prox_grad_step) run as one device-resident loop, with lambda continuation and
+ * a stopping test on the iterates; the host issues one graph launch and is not
+ * involved again until the run ends.
+ *
+ * Stage k = 0, 1, ... solves at lambda_k = max(lambda, lambda0 eta^k); the stage
+ * with lambda_k == lambda is the last. A stage repeats proximal-gradient steps
+ *   Z = X + step P_Omega(M - X);  X <- A_{step lambda_k}(Z)
+ * until the relative change rho = ||X_new - X_old||_F / ||P_Omega(M)||_F (FP64,
+ * against the data's scale so that it stays meaningful for a zero or nearly zero
+ * iterate; 0 when both norms are zero) is <= tol, or until it has run stage_steps
+ * steps (stages before the last; 0 = no cap). The run ends when the last stage stops, after max_steps steps in all,
+ * or at the first solve whose device-side status is not SVT_OK. At a fixed lambda
+ * the step map is non-expansive, so ||X_new - X_old||_F does not grow within a stage,
+ * and ||P_Omega(M - X_new)||_2 <= lambda_k + (1 + 1/step) ||X_new - X_old||_F.
+ *
+ * The loop is a CUDA graph: one conditional WHILE node per stage whose body is the
+ * masked gradient step (which also copies X to Xprev), the solve's launches, an FP64
+ * reduction of ||X - Xprev||_F^2, and a one-thread kernel that updates
+ * *d_stats and decides whether the body runs again. Graphs are cached on the context
+ * per argument set (the four most recent); a repeated call relaunches its graph.
+ *
+ *   X, M, mask, Z: as svt_prox_grad_step (X: the starting point, overwritten with the
+ *     result).
+ *   Xprev: m x n FP32 device scratch (ldp >= n), overlapping none of X, M, mask, Z.
+ *   p: the parameters below. opt: as svt_polar_ex (NULL = defaults).
+ *   d_stats: device, 8-byte aligned, written by the run (any earlier contents are
+ *     ignored); valid once the stream reaches the end of the run.
+ * Asynchronous on `stream`. The context's workspace is in use until the run ends.
+ * svt_ctx_launch_count counts the run as one launch.
+ * Errors (before any launch): SVT_ERR_INVALID (pointers, sizes, leading dimensions,
+ * overlapping buffers, parameters outside the ranges below, more than 64 stages,
+ * options), SVT_ERR_OOM (workspace), SVT_ERR_BUSY (serving active),
+ * SVT_ERR_UNSUPPORTED (sizes, or a driver without conditional graph nodes),
+ * SVT_ERR_CUDA.
+ */
+typedef struct {
+    float lambda;     /* target lambda, finite, >= 0 */
+    float lambda0;    /* lambda of the first stage, finite, >= lambda (== lambda: one stage) */
+    float eta;        /* stage factor, in (0, 1) when lambda0 > lambda (else ignored) */
+    float step;       /* proximal-gradient step, finite, > 0 (<= 1 does not increase F) */
+    float tol;        /* relative-change tolerance, finite, >= 0 */
+    int max_steps;    /* steps in all stages, >= 0 */
+    int stage_steps;  /* steps per stage before the last, >= 0 (0 = no cap) */
+} svt_completion_params;
+
+typedef struct {
+    int steps;          /* proximal-gradient steps taken */
+    int stages;         /* stages entered */
+    int stage_steps;    /* steps of the last stage entered */
+    int status;         /* SVT_OK, or the first solve's non-OK device-side status */
+    int solve_status;   /* device-side status of the last solve */
+    int reserved;
+    double lambda;      /* lambda of the last step */
+    double rel_change;  /* rho of the last step */
+    double diff2;       /* reduction accumulator (zero between steps) */
+    double data2;       /* ||P_Omega(M)||_F^2 */
+} svt_completion_stats;
+
+svt_status svt_complete(svt_ctx_t ctx, float *X, int64_t ldx, const float *M, int64_t ldm,
+                        const uint8_t *mask, int64_t ldw, float *Z, int64_t ldz, float *Xprev,
+                        int64_t ldp, int64_t m, int64_t n, const svt_completion_params *p,
+                        const svt_options *opt, svt_completion_stats *d_stats, void *stream);
+
 /* svt_debug_gemm_bf16 with an explicit tile-width code: 0 = automatic (as
  * svt_debug_gemm_bf16), 128, 256, or 512 (a cluster of two CTAs per 256 x 256
  * tile, tcgen05 cta_group::2). Errors: as above; SVT_ERR_INVALID on another tile. */

@@ -75,10 +75,11 @@ def complete_continuation(m: np.ndarray, mask: np.ndarray, lam: float, lam0: flo
 
     Stage k (k = 0, 1, ...) solves at lambda_k = max(lam, lam0 eta^k); the stage whose
     lambda_k equals lam is the last. Each stage runs proximal-gradient steps until the
-    relative change rho = ||X_new - X_old||_F / ||X_new||_F (0 when both are zero,
-    infinity when only X_new is zero) is <= tol, or until it has run stage_steps steps
-    (non-final stages only; 0 = no cap). The run ends when the last stage stops or after
-    max_steps steps in total.
+    relative change rho = ||X_new - X_old||_F / ||P_Omega(M)||_F (measured against the
+    data's scale, so that it stays meaningful when the iterate is zero or nearly so; 0
+    when both norms are zero, infinity when only the data's is) is <= tol, or until it
+    has run stage_steps steps (non-final stages only; 0 = no cap). The run ends when the
+    last stage stops or after max_steps steps in total.
 
     At a fixed lambda the step map is non-expansive, so ||X_new - X_old||_F never grows
     within a stage, and a small change bounds the optimality residual of X_new (see the
@@ -92,6 +93,7 @@ def complete_continuation(m: np.ndarray, mask: np.ndarray, lam: float, lam0: flo
         raise ValueError("eta must lie in (0, 1) when lam0 > lam")
     m = np.asarray(m, dtype=np.float64)
     x = np.zeros_like(m) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
+    scale = float(np.linalg.norm(np.where(mask != 0, m, 0.0)))
     info = {"steps": 0, "stages": 0, "rel_change": 0.0, "lambdas": [], "changes": [],
             "rhos": [], "stage_of_step": []}
     k = 0
@@ -103,8 +105,7 @@ def complete_continuation(m: np.ndarray, mask: np.ndarray, lam: float, lam0: flo
         while info["steps"] < max_steps:
             x_new = prox_grad_step(x, m, mask, lam_k, step)
             d = float(np.linalg.norm(x_new - x))
-            nx = float(np.linalg.norm(x_new))
-            rho = d / nx if nx > 0 else (0.0 if d == 0 else np.inf)
+            rho = d / scale if scale > 0 else (0.0 if d == 0 else np.inf)
             x = x_new
             taken += 1
             info["steps"] += 1

@@ -8,5 +8,5 @@ The compute path is the C-ABI library libsvt.so (include/svt.h); this package
 is its Python binding.
 """
 from .binding import (BF16, FP32, FP64, Context, Matrix, Options, SVTError,  # noqa: F401
-                      EXPORTS, lib, make_options, polar_noalloc, schedule_coeffs, status_str,
-                      workspace_bytes)
+                      EXPORTS, lib, make_options, polar_noalloc, read_completion_stats,
+                      schedule_coeffs, status_str, workspace_bytes)

@@ -40,7 +40,7 @@ EXPORTS = [
     "svt_ctx_sync", "svt_schedule_coeffs", "svt_debug_gemm_bf16", "svt_debug_gemm_bf16_ex",
     "svt_ctx_launch_count",
     "svt_ctx_profile", "svt_ctx_profile_read", "svt_polar_noalloc", "svt_autotune",
-    "svt_prox_grad_step",
+    "svt_prox_grad_step", "svt_complete",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -56,6 +56,32 @@ class Matrix(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
                 ("lda", ctypes.c_int64), ("tau", ctypes.c_float), ("Y", ctypes.c_void_p),
                 ("ldy", ctypes.c_int64), ("opt", Options), ("d_status", ctypes.c_void_p)]
+
+
+class CompletionParams(ctypes.Structure):
+    _fields_ = [("lam", ctypes.c_float), ("lam0", ctypes.c_float), ("eta", ctypes.c_float),
+                ("step", ctypes.c_float), ("tol", ctypes.c_float), ("max_steps", ctypes.c_int),
+                ("stage_steps", ctypes.c_int)]
+
+
+class CompletionStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("stages", ctypes.c_int), ("stage_steps", ctypes.c_int),
+                ("status", ctypes.c_int), ("solve_status", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("lam", ctypes.c_double), ("rel_change", ctypes.c_double),
+                ("diff2", ctypes.c_double), ("data2", ctypes.c_double)]
+
+
+COMPLETION_STATS_BYTES = ctypes.sizeof(CompletionStats)
+
+
+def read_completion_stats(stats) -> dict:
+    """The svt_completion_stats a run wrote into the CUDA byte tensor `stats` (copies it
+    to the host, which waits for the run)."""
+    raw = bytes(stats.cpu().numpy().tobytes())[:COMPLETION_STATS_BYTES]
+    c = CompletionStats.from_buffer_copy(raw)
+    return {"steps": c.steps, "stages": c.stages, "stage_steps": c.stage_steps,
+            "status": c.status, "lam": c.lam, "rel_change": c.rel_change,
+            "data_norm": c.data2 ** 0.5}
 
 
 class SVTError(RuntimeError):
@@ -101,6 +127,14 @@ def lib():
                                           ctypes.POINTER(ctypes.c_double)]
         L.svt_debug_gemm_bf16.argtypes = [vp, i32, vp, vp, vp, vp, i64, i64, i64, i64, i64, vp,
                                           i64, i32, vp]
+        L.svt_debug_gemm_bf16_ex.argtypes = [vp, i32, vp, vp, vp, vp, i64, i64, i64, i64, i64,
+                                             vp, i64, i32, i32, vp]
+        L.svt_prox_grad_step.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, i64, i64, i64,
+                                         ctypes.c_float, ctypes.c_float, ctypes.POINTER(Options),
+                                         vp, vp]
+        L.svt_complete.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, i64, i64,
+                                   ctypes.POINTER(CompletionParams), ctypes.POINTER(Options), vp,
+                                   vp]
         L.svt_ctx_launch_count.argtypes = [vp]
         L.svt_ctx_launch_count.restype = ctypes.c_uint64
         L.svt_ctx_profile.argtypes = [vp, i32]
@@ -297,6 +331,50 @@ class Context:
             self.prox_grad_step(X, M, mask, lam, Z=Z, step=step, status=status, stream=stream,
                                 **opts)
         return X
+
+    def complete_on_device(self, M, mask, lam: float, max_steps: int, lam0: float | None = None,
+                           eta: float = 0.5, tol: float = 0.0, stage_steps: int = 0,
+                           step: float = 1.0, X=None, Z=None, Xprev=None, stats=None,
+                           stream=None, **opts):
+        """Proximal-gradient completion as one device-resident loop (svt_complete):
+        lambda continuation from lam0 (None: lam, one stage) by factor eta down to lam,
+        stages ending when ||X_new - X_old||_F / ||X_new||_F <= tol or after stage_steps
+        steps, at most max_steps steps in all. X is the starting point (zeros if None)
+        and receives the result. Returns (X, stats): stats is a CUDA byte tensor holding
+        svt_completion_stats (read_completion_stats parses it)."""
+        import torch
+        m_ptr, m, n, ldm = _f32_matrix(M, "M")
+        if (not isinstance(mask, torch.Tensor) or mask.dtype != torch.uint8 or not mask.is_cuda
+                or tuple(mask.shape) != (m, n) or mask.stride(1) != 1):
+            raise ValueError("mask must be a row-major CUDA uint8 tensor of M's shape")
+        if X is None:
+            X = torch.zeros((m, n), dtype=torch.float32, device=M.device)
+        if Z is None:
+            Z = torch.empty((m, n), dtype=torch.float32, device=M.device)
+        if Xprev is None:
+            Xprev = torch.empty((m, n), dtype=torch.float32, device=M.device)
+        if stats is None:
+            stats = torch.zeros(COMPLETION_STATS_BYTES, dtype=torch.uint8, device=M.device)
+        if stats.numel() < COMPLETION_STATS_BYTES or stats.data_ptr() % 8:
+            raise ValueError("stats must hold svt_completion_stats, 8-byte aligned")
+        ptrs = []
+        for t, name in ((X, "X"), (Z, "Z"), (Xprev, "Xprev")):
+            p, tm, tn, ld = _f32_matrix(t, name)
+            if (tm, tn) != (m, n):
+                raise ValueError(f"{name} has the wrong shape")
+            ptrs.append((p, ld))
+        prm = CompletionParams(float(lam), float(lam if lam0 is None else lam0), float(eta),
+                               float(step), float(tol), int(max_steps), int(stage_steps))
+        o = make_options(**opts)
+        self.ensure_workspace(workspace_bytes(m, n, **opts))
+        _check(lib().svt_complete(self.handle, ctypes.c_void_p(ptrs[0][0]), ptrs[0][1],
+                                  ctypes.c_void_p(m_ptr), ldm, ctypes.c_void_p(mask.data_ptr()),
+                                  mask.stride(0), ctypes.c_void_p(ptrs[1][0]), ptrs[1][1],
+                                  ctypes.c_void_p(ptrs[2][0]), ptrs[2][1], m, n,
+                                  ctypes.byref(prm), ctypes.byref(o),
+                                  ctypes.c_void_p(stats.data_ptr()),
+                                  ctypes.c_void_p(_stream_ptr(stream))), "svt_complete")
+        return X, stats
 
     def autotune(self, A, tau: float, out=None, reps: int = 2, stream=None, **opts):
         """Pick the product kernel's tile width per launch for this shape and options

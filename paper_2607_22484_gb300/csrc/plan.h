@@ -166,10 +166,15 @@ struct CallArgs {
     float *Y;
     int64_t ldy;
     svt_status *d_status;
+    // Launches recorded into a CUDA graph body: no fused-table upload (the caller
+    // uploads it before launching the graph), no event records, no launch count.
+    bool in_graph = false;
 };
 
 svt_status validate(const float *A, int64_t m, int64_t n, int64_t lda, float tau, const float *Y,
                     int64_t ldy);
+
+struct CompletionGraph;  // completion.cu
 
 } // namespace svt
 
@@ -195,6 +200,9 @@ struct svt_ctx {
     // Which grouped-batch plan's device tables are intact in the workspace (any
     // other use of the workspace resets it; the batch then re-uploads its tables).
     const void *table_owner = nullptr;
+    // Cached device-resident completion loops (completion.cu), most recent last.
+    std::vector<svt::CompletionGraph *> completion_graphs;
+    cudaStream_t capture_stream = nullptr;  // private stream for graph capture
 };
 
 namespace svt {
@@ -212,6 +220,14 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
                    size_t last, int sms = 0);
 // Read the plan's internal status word back to host memory (async on s).
 svt_status plan_status_copy(svt_ctx *ctx, const Plan &P, int *host_dst, cudaStream_t s);
+// The plan a solve of this shape and these options uses (tuned, explicit or automatic
+// tile width), as svt_polar_ex looks it up (under ctx->mu).
+svt_status plan_for_solve(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, Plan **out,
+                          std::shared_ptr<Plan> *keep = nullptr);
+// Refresh the plan's fused-launch table in the workspace from its host image (async on s).
+svt_status upload_fused_table(svt_ctx *ctx, Plan &P, cudaStream_t s);
+// Release the context's cached completion graphs (after the device is idle).
+void completion_release(svt_ctx *ctx);
 void serve_shutdown(svt_ctx *ctx);
 bool serve_busy(svt_ctx *ctx);
 } // namespace svt

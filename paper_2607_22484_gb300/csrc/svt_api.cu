@@ -707,6 +707,7 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
     int cur_final = P.opt.iters % 2;
     int launched = 0;
     const bool fused = P.fused && first == 0 && last >= P.ops.size();
+    const bool prof = ctx->profile && !a.in_graph;
     bool fused_done = false;
     ctx->table_owner = nullptr;  // this solve overwrites part of the workspace
     for (size_t oi = first; oi < last && oi < P.ops.size(); ++oi) {
@@ -716,8 +717,7 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
                 continue;
             fused_done = true;
             // The table region is shared with other plans: refresh it from the host image.
-            if (cudaMemcpyAsync(const_cast<TcProblem *>(P.fused_launch.gtab), P.h_fused,
-                                P.fused_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            if (!a.in_graph && upload_fused_table(ctx, P, s) != SVT_OK)
                 return SVT_ERR_CUDA;
             TcLaunch l = P.fused_launch;
             l.call_inline.A = a.A;
@@ -727,7 +727,7 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
             l.call_inline.tau = a.tau;
             l.call_inline.d_status = a.d_status;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (ctx->profile) {
+            if (prof) {
                 if (ctx->prof_next + 2 > ctx->prof_pool.size()) {
                     for (int k = 0; k < 64; ++k) {
                         cudaEvent_t ev;
@@ -741,7 +741,7 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
                 cudaEventRecord(e0, s);
             }
             err = tc_gemm_launch_fused(l, P.fused_bn, P.fused_tiles, grid_sms, s, P.uses_strips);
-            if (ctx->profile) {
+            if (prof) {
                 cudaEventRecord(e1, s);
                 ctx->prof_pending.push_back({e0, e1, P.fused_flops});
             }
@@ -796,7 +796,7 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
                         e.alpha = -(double)a.tau;
                 }
             cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (ctx->profile) {
+            if (prof) {
                 if (ctx->prof_next + 2 > ctx->prof_pool.size()) {
                     for (int k = 0; k < 64; ++k) {
                         cudaEvent_t ev;
@@ -810,7 +810,7 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
                 cudaEventRecord(e0, s);
             }
             err = tc_gemm_launch(l, op.bn, grid_sms, s);
-            if (ctx->profile) {
+            if (prof) {
                 cudaEventRecord(e1, s);
                 ctx->prof_pending.push_back({e0, e1, P.tc_flops[op.idx]});
             }
@@ -859,8 +859,20 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
         if (err != cudaSuccess)
             return SVT_ERR_CUDA;
     }
-    ctx->launches += (uint64_t)launched;
+    if (!a.in_graph)
+        ctx->launches += (uint64_t)launched;
     return SVT_OK;
+}
+
+svt_status upload_fused_table(svt_ctx *ctx, Plan &P, cudaStream_t s)
+{
+    if (!P.fused)
+        return SVT_OK;
+    ctx->table_owner = nullptr;
+    return cudaMemcpyAsync(const_cast<TcProblem *>(P.fused_launch.gtab), P.h_fused, P.fused_bytes,
+                           cudaMemcpyHostToDevice, s) == cudaSuccess
+               ? SVT_OK
+               : SVT_ERR_CUDA;
 }
 
 svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, int sms)
@@ -1056,6 +1068,13 @@ svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_
     return SVT_OK;
 }
 
+svt_status plan_for_solve(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, Plan **out,
+                          std::shared_ptr<Plan> *keep)
+{
+    const int fbn = r.tile ? r.tile : (ctx->tuning.count(tune_key(m, n, r)) ? -1 : 0);
+    return get_plan(ctx, m, n, r, 0, ctx->ws_bytes, out, fbn, keep);
+}
+
 svt_status plan_status_copy(svt_ctx *ctx, const Plan &P, int *host_dst, cudaStream_t s)
 {
     const int *src = reinterpret_cast<const int *>(ctx->ws + P.ws_base + P.lay.status);
@@ -1178,6 +1197,7 @@ svt_status svt_ctx_destroy(svt_ctx_t ctx)
     serve_shutdown(ctx);
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    completion_release(ctx);
     for (cudaEvent_t e : ctx->prof_pool)
         cudaEventDestroy(e);
     delete ctx;
@@ -1204,8 +1224,7 @@ svt_status svt_polar_ex(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int
     if (cudaSetDevice(ctx->device) != cudaSuccess)
         return SVT_ERR_CUDA;
     Plan *plan = nullptr;
-    const int fbn = r.tile ? r.tile : (ctx->tuning.count(tune_key(m, n, r)) ? -1 : 0);
-    st = get_plan(ctx, m, n, r, 0, ctx->ws_bytes, &plan, fbn);
+    st = plan_for_solve(ctx, m, n, r, &plan);
     if (st != SVT_OK)
         return st;
     CallArgs a{A, lda, tau, Y, ldy, d_status};

@@ -61,3 +61,52 @@ def test_schedule_ns3_and_errors():
         pkg.schedule_coeffs("pe5", 3, ell0=0.0)
     with pytest.raises(pkg.SVTError):
         pkg.schedule_coeffs("pe5", -1)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the header's sizes and field offsets
+    (a C program compiled against include/svt.h prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {
+        "svt_options": (pkg.Options, ["iters", "prec", "schedule", "norm", "ell0", "delta",
+                                      "polish", "mode", "fuse", "hp_steps", "tile"]),
+        "svt_matrix": (pkg.Matrix, ["A", "m", "n", "lda", "tau", "Y", "ldy", "opt", "d_status"]),
+        "svt_completion_params": (pkg.binding.CompletionParams,
+                                  ["lambda", "lambda0", "eta", "step", "tol", "max_steps",
+                                   "stage_steps"]),
+        "svt_completion_stats": (pkg.binding.CompletionStats,
+                                 ["steps", "stages", "stage_steps", "status", "solve_status",
+                                  "reserved", "lambda", "rel_change", "diff2", "data2"]),
+    }
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "svt.h"', "int main(void) {"]
+    for name, (_, fields) in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f in fields:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run(
+        [str(exe)], check=True, capture_output=True, text=True).stdout.splitlines())
+    for name, (cls, fields) in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, (pyname, _) in zip(fields, cls._fields_):
+            assert int(got[f"{name}.{f}"]) == getattr(cls, pyname).offset, (name, f)
+
+
+def test_complete_rejects_null_arguments_on_the_host():
+    """svt_complete validates its arguments before touching the device."""
+    import ctypes
+    lib = pkg.lib()
+    prm = pkg.binding.CompletionParams(0.1, 0.1, 0.5, 1.0, 0.0, 5, 0)
+    st = lib.svt_complete(None, None, 4, None, 4, None, 4, None, 4, None, 4, 4, 4,
+                          ctypes.byref(prm), None, None, None)
+    assert pkg.status_str(st) == "SVT_ERR_INVALID"

@@ -16,6 +16,12 @@ M = L R^T with L, R ~ N(0,1)^{256 x 5}, ||M||_2 ~ 10, a Bernoulli(0.2) mask.
   stay within T times the per-solve error of the oracle's iterate.
 * The configured threshold lambda = 0.02 ||P_Omega(M)||_2 (no gap): the loop's
   objective and recovery error are compared with the oracle's.
+* The device-resident loop (svt_complete: lambda continuation, relative-change
+  stopping test, one graph launch): its iterates against the host loop and the
+  oracle, its statistics against the oracle's stage rule, and the residual bound at
+  its stop. With E the solve's error in the last step (FP32 tier: <= 1e-4 of the
+  result here), ||P_Omega(M - X)||_2 <= lambda + (1 + 1/h) ||X - X_prev||_F + ||E||_F / h;
+  the relative change is ||X - X_prev||_F / ||P_Omega(M)||_F.
 """
 import numpy as np
 import pytest
@@ -152,3 +158,156 @@ def test_invalid_arguments(ctx, inst):
         ctx.prox_grad_step(X, M, W, float("inf"))
     with pytest.raises(ValueError):
         ctx.prox_grad_step(X, M, W.float(), lam_gap)     # mask must be bytes
+
+
+# --- the device-resident loop (svt_complete)
+
+def _stats(st):
+    return pkg.read_completion_stats(st)
+
+
+def test_device_loop_fixed_steps_matches_host_loop(ctx, inst):
+    """One stage, tol 0: the loop runs max_steps steps of the same step as the host
+    loop of svt_prox_grad_step."""
+    m, mask, lam_gap, _ = inst
+    M, W = _dev(m, mask)
+    before = ctx.launch_count()
+    X, st = ctx.complete_on_device(M, W, lam_gap, 6, iters=20, prec="fp32")
+    assert ctx.launch_count() == before + 1
+    s = _stats(st)
+    assert (s["steps"], s["stages"], s["stage_steps"], s["status"]) == (6, 1, 6, 0)
+    assert s["lam"] == pytest.approx(lam_gap, rel=1e-6)
+    Xh = ctx.complete(M, W, lam_gap, 6, iters=20, prec="fp32")
+    torch.cuda.synchronize()
+    assert oracle.relerr(X.cpu().numpy().astype(np.float64),
+                         Xh.cpu().numpy().astype(np.float64)) < 1e-5
+    # the last relative change is the one of the iterates
+    x5 = ctx.complete(M, W, lam_gap, 5, iters=20, prec="fp32").cpu().numpy().astype(np.float64)
+    x6 = X.cpu().numpy().astype(np.float64)
+    scale = np.linalg.norm(np.where(mask != 0, m.astype(np.float64), 0.0))
+    assert s["data_norm"] == pytest.approx(scale, rel=1e-12)
+    rho = np.linalg.norm(x6 - x5) / scale
+    assert abs(s["rel_change"] - rho) < 0.05 * rho + 2e-6, (s["rel_change"], rho)
+
+
+def test_device_loop_continuation_against_the_oracle(ctx, inst):
+    """Continuation from 2.5 times the gapped lambda down to it, tol 1e-4: same stage
+    count as the oracle's rule, the stop's residual bound, and the oracle's minimum."""
+    m, mask, lam_gap, _ = inst
+    m64 = m.astype(np.float64)
+    lam0, eta, tol, cap = 2.5 * lam_gap, 0.5, 1e-4, 8
+    M, W = _dev(m, mask)
+    X, st = ctx.complete_on_device(M, W, lam_gap, 120, lam0=lam0, eta=eta, tol=tol,
+                                   stage_steps=cap, iters=20, prec="fp32")
+    s = _stats(st)
+    x = X.cpu().numpy().astype(np.float64)
+    xo, info = oc.complete_continuation(m64, mask, lam_gap, lam0, eta, tol, 120, stage_steps=cap)
+    print(f"device loop: {s}; oracle: steps {info['steps']}, stages {info['stages']}, "
+          f"rho {info['rel_change']:.2e}")
+    assert s["status"] == 0
+    assert s["stages"] == info["stages"]
+    assert s["lam"] == pytest.approx(lam_gap, rel=1e-6)
+    assert s["steps"] < 120 and s["rel_change"] <= tol
+    assert abs(s["steps"] - info["steps"]) <= 4, (s["steps"], info["steps"])
+    g = np.where(mask != 0, m64 - x, 0.0)
+    r = s["rel_change"] * s["data_norm"]
+    bound = lam_gap + 2.0 * r + 1e-4 * np.linalg.norm(x)
+    assert np.linalg.norm(g, 2) <= bound, (np.linalg.norm(g, 2), bound)
+    f_gpu = oc.objective(x, m64, mask, lam_gap)
+    f_ref = oc.objective(xo, m64, mask, lam_gap)
+    assert abs(f_gpu - f_ref) < 1e-4 * f_ref, (f_gpu, f_ref)
+
+
+def test_device_loop_stage_caps(ctx, inst):
+    """tol 0 and a cap of 2 steps per stage: 2 + 2 + the rest in the last stage (the
+    stage lambdas stay below sigma_max of P_Omega(M), so no stage's iterate stays
+    exactly put, which would end it at tol 0)."""
+    m, mask, lam_gap, _ = inst
+    M, W = _dev(m, mask)
+    _, st = ctx.complete_on_device(M, W, lam_gap, 9, lam0=1.4 * lam_gap, eta=0.8,
+                                   stage_steps=2, iters=12, prec="bf16")
+    s = _stats(st)
+    assert (s["steps"], s["stages"], s["stage_steps"], s["status"]) == (9, 3, 5, 0)
+    _, info = oc.complete_continuation(m.astype(np.float64), mask, lam_gap, 1.4 * lam_gap, 0.8,
+                                       0.0, 9, stage_steps=2)
+    assert [info["stage_of_step"].count(k) for k in range(3)] == [2, 2, 5]
+
+
+def test_device_loop_bf16_against_the_oracle(ctx, inst):
+    """BF16 tier, one stage, 10 steps: within the per-step operand-scale bound of the
+    oracle's iterates (as the host loop)."""
+    m, mask, lam_gap, _ = inst
+    M, W = _dev(m, mask)
+    X, st = ctx.complete_on_device(M, W, lam_gap, 10, iters=20, prec="bf16")
+    s = _stats(st)
+    assert (s["steps"], s["status"]) == (10, 0)
+    m64 = m.astype(np.float64)
+    x, bound = np.zeros_like(m64), 0.0
+    for _ in range(10):
+        z = np.where(mask != 0, m64, x)
+        x = oc.prox_grad_step(x, m64, mask, lam_gap)
+        bound += _bound("bf16", x, z)
+    err = np.linalg.norm(X.cpu().numpy().astype(np.float64) - x)
+    assert err < bound, (err, bound)
+
+
+def test_device_loop_zero_steps_and_relaunch(ctx, inst):
+    m, mask, lam_gap, _ = inst
+    M, W = _dev(m, mask)
+    x0 = torch.from_numpy(
+        (np.random.default_rng(5).standard_normal(m.shape) * 0.01).astype(np.float32)).cuda()
+    X = x0.clone()
+    _, st = ctx.complete_on_device(M, W, lam_gap, 0, X=X, iters=20, prec="fp32")
+    s = _stats(st)
+    assert (s["steps"], s["stages"], s["status"]) == (0, 0, 0)
+    assert torch.equal(X, x0)
+    # the same arguments twice: the cached graph runs again from the reset start
+    Z = torch.empty_like(M)
+    P = torch.empty_like(M)
+    outs = []
+    for _ in range(2):
+        X.copy_(x0)
+        ctx.complete_on_device(M, W, lam_gap, 4, X=X, Z=Z, Xprev=P, stats=st, iters=20,
+                               prec="fp32")
+        outs.append(X.clone())
+        assert _stats(st)["steps"] == 4
+    assert oracle.relerr(outs[0].cpu().numpy().astype(np.float64),
+                         outs[1].cpu().numpy().astype(np.float64)) < 1e-6
+
+
+def test_device_loop_stops_on_a_nonfinite_solve(ctx, inst):
+    m, mask, lam_gap, _ = inst
+    mm = m.copy()
+    i, j = np.argwhere(mask != 0)[0]
+    mm[i, j] = np.nan
+    M, W = _dev(mm, mask)
+    _, st = ctx.complete_on_device(M, W, lam_gap, 5, iters=8, prec="bf16")
+    s = _stats(st)
+    assert s["status"] == pkg.binding.ERR_NONFINITE
+    assert s["steps"] == 1
+
+
+def test_device_loop_invalid_arguments(ctx, inst):
+    m, mask, lam_gap, _ = inst
+    M, W = _dev(m, mask)
+    X = torch.zeros_like(M)
+    bad = [
+        dict(lam0=0.5 * lam_gap),                 # lam0 < lam
+        dict(lam0=2 * lam_gap, eta=1.0),          # no decrease
+        dict(lam0=2 * lam_gap, eta=0.0),
+        dict(tol=-1.0),
+        dict(stage_steps=-1),
+        dict(step=0.0),
+    ]
+    for kw in bad:
+        with pytest.raises(pkg.SVTError):
+            ctx.complete_on_device(M, W, lam_gap, 3, X=X, **kw)
+    with pytest.raises(pkg.SVTError):                 # more than 64 stages
+        ctx.complete_on_device(M, W, 0.0, 3, lam0=1.0, eta=0.5, X=X)
+    with pytest.raises(pkg.SVTError):                 # negative step count
+        ctx.complete_on_device(M, W, lam_gap, -1, X=X)
+    with pytest.raises(pkg.SVTError):                 # Xprev aliases X
+        ctx.complete_on_device(M, W, lam_gap, 3, X=X, Xprev=X)
+    st = torch.zeros(pkg.binding.COMPLETION_STATS_BYTES + 8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ValueError):                   # misaligned statistics
+        ctx.complete_on_device(M, W, lam_gap, 3, X=X, stats=st[1:])
