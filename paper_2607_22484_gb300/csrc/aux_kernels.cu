@@ -24,85 +24,6 @@ __device__ __forceinline__ void set_status(int *status, svt_status s)
         atomicCAS(status, 0, (int)s);
 }
 
-// Column norms (wide = 0): block (32, 8) covers 32 columns and kRowsPerBlock rows.
-constexpr int kRowsPerBlock = 256;
-
-// Block (bx, by) of the column-norm reduction; threads (tx, ty) in 32 x 8.
-__device__ __forceinline__ void colnorm_block(const float *__restrict__ A, int64_t m, int64_t n,
-                                              int64_t lda, double *colnorm2, double *scal,
-                                              int *status, int bx, int by, int tx, int ty)
-{
-    __shared__ double part[8][33];
-    const int64_t col = (int64_t)bx * 32 + tx;
-    const int64_t r0 = (int64_t)by * kRowsPerBlock;
-    const int64_t r1 = (m < r0 + kRowsPerBlock) ? m : r0 + kRowsPerBlock;
-    double s = 0.0;
-    bool finite = true;
-    if (col < n) {
-        for (int64_t r = r0 + ty; r < r1; r += 8) {
-            float a = A[r * lda + col];
-            finite &= isfinite(a);
-            s += (double)a * (double)a;
-        }
-    }
-    if (!finite)
-        set_status(status, SVT_ERR_NONFINITE);
-    part[ty][tx] = s;
-    __syncthreads();
-    if (ty == 0) {
-        double t = 0.0;
-        for (int i = 0; i < 8; ++i)
-            t += part[i][tx];
-        if (col < n)
-            atomicAdd(&colnorm2[col], t);
-        // block total for ||A||_F^2
-        for (int o = 16; o > 0; o >>= 1)
-            t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (tx == 0)
-            atomicAdd(&scal[SC_NRM_A2], t);
-    }
-}
-
-__global__ void ingest_colnorm_kernel(const float *__restrict__ A, int64_t m, int64_t n,
-                                      int64_t lda, double *colnorm2, double *scal, int *status)
-{
-    colnorm_block(A, m, n, lda, colnorm2, scal, status, blockIdx.x, blockIdx.y, threadIdx.x,
-                  threadIdx.y);
-}
-
-// Row norms (wide = 1): one warp per row.
-// Row norms of rows 8 bx .. 8 bx + 7 (one warp per row, 256 threads).
-__device__ __forceinline__ void rownorm_block(const float *__restrict__ A, int64_t m, int64_t n,
-                                              int64_t lda, double *colnorm2, double *scal,
-                                              int *status, int bx, int tid)
-{
-    const int64_t row = (int64_t)bx * 8 + tid / 32;
-    const int lane = tid & 31;
-    if (row >= m)
-        return;
-    double s = 0.0;
-    bool finite = true;
-    for (int64_t c = lane; c < n; c += 32) {
-        float a = A[row * lda + c];
-        finite &= isfinite(a);
-        s += (double)a * (double)a;
-    }
-    if (!finite)
-        set_status(status, SVT_ERR_NONFINITE);
-    for (int o = 16; o > 0; o >>= 1)
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-        colnorm2[row] = s;
-        atomicAdd(&scal[SC_NRM_A2], s);
-    }
-}
-
-__global__ void ingest_rownorm_kernel(const float *__restrict__ A, int64_t m, int64_t n,
-                                      int64_t lda, double *colnorm2, double *scal, int *status)
-{
-    rownorm_block(A, m, n, lda, colnorm2, scal, status, blockIdx.x, threadIdx.x);
-}
-
 // alpha = 2^e with e = round(log2 ||A||_F) (1 for a zero matrix): dividing by it is exact.
 __device__ __forceinline__ double pow2_alpha(double nrm2)
 {
@@ -115,65 +36,305 @@ __device__ __forceinline__ double pow2_alpha(double nrm2)
     return ldexp(1.0, e);
 }
 
-// 32 x 32 tile of A -> same-orientation and transposed copies of A / alpha.
-template <bool F64>
-__device__ __forceinline__ void split_block(const float *__restrict__ A, int64_t m, int64_t n,
-                                            int64_t lda, float tau, void *xs_hi, void *xs_lo,
-                                            int64_t ld_s, void *xt_hi, void *xt_lo, int64_t ld_t,
-                                            double *scal, int bx, int by, int tx, int ty)
+// ---- ingest: column (or row) norms and the split into scaled copies
+//
+// The same block functions serve the single-matrix kernels and the grouped
+// kernels of batches, so that a matrix is ingested identically either way. Rows
+// are read with 16-byte loads where A and lda allow (vec), with the same thread
+// mapping and summation order otherwise. Squares are summed in FP32 over four
+// values and in FP64 beyond; the FP64 tier (F64SUM) sums every square in FP64.
+
+constexpr int kColRows4 = 128;  // rows per block of the column norms
+
+// Column norms (tall input): 256 threads; block (bx, by) covers 128 columns (32
+// lanes x 4) and kColRows4 rows, warp w taking rows r0 + w, r0 + w + 8, ...
+template <bool F64SUM>
+__device__ __forceinline__ void colnorm4_block(const float *__restrict__ A, int64_t m, int64_t n,
+                                               int64_t lda, double *colnorm2, double *scal,
+                                               int *status, int bx, int by, bool vec)
 {
-    __shared__ float tile[32][33];
+    __shared__ double part[8][129];
+    __shared__ double wsum[4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t c0 = (int64_t)bx * 128 + lane * 4;
+    const int64_t r0 = (int64_t)by * kColRows4;
+    const int64_t r1 = (m < r0 + kColRows4) ? m : r0 + kColRows4;
+    const bool full = vec && c0 + 3 < n;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    bool finite = true;
+    if (c0 < n) {
+        for (int64_t r = r0 + w; r < r1; r += 32) {
+            float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t rr = r + 8 * u;
+                if (rr < r1) {
+                    const float *a = A + rr * lda + c0;
+                    float4 v;
+                    if (full) {
+                        v = *reinterpret_cast<const float4 *>(a);
+                    } else {
+                        v.x = a[0];
+                        v.y = c0 + 1 < n ? a[1] : 0.f;
+                        v.z = c0 + 2 < n ? a[2] : 0.f;
+                        v.w = c0 + 3 < n ? a[3] : 0.f;
+                    }
+                    finite &= isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w);
+                    if (F64SUM) {
+                        s0 += (double)v.x * v.x;
+                        s1 += (double)v.y * v.y;
+                        s2 += (double)v.z * v.z;
+                        s3 += (double)v.w * v.w;
+                    } else {
+                        p0 = fmaf(v.x, v.x, p0);
+                        p1 = fmaf(v.y, v.y, p1);
+                        p2 = fmaf(v.z, v.z, p2);
+                        p3 = fmaf(v.w, v.w, p3);
+                    }
+                }
+            }
+            if (!F64SUM) {
+                s0 += p0;
+                s1 += p1;
+                s2 += p2;
+                s3 += p3;
+            }
+        }
+    }
+    if (!finite)
+        set_status(status, SVT_ERR_NONFINITE);
+    part[w][lane * 4 + 0] = s0;
+    part[w][lane * 4 + 1] = s1;
+    part[w][lane * 4 + 2] = s2;
+    part[w][lane * 4 + 3] = s3;
+    __syncthreads();
+    if (threadIdx.x < 128) {
+        double t = 0.0;
+        for (int i = 0; i < 8; ++i)
+            t += part[i][threadIdx.x];
+        const int64_t col = (int64_t)bx * 128 + threadIdx.x;
+        if (col < n && t != 0.0)
+            atomicAdd(&colnorm2[col], t);
+        for (int o = 16; o > 0; o >>= 1)
+            t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0)
+            wsum[w] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double b = wsum[0] + wsum[1] + wsum[2] + wsum[3];
+        if (b != 0.0)
+            atomicAdd(&scal[SC_NRM_A2], b);
+    }
+}
+
+// Row norms (wide input): one warp per row, rows 8 bx .. 8 bx + 7 (256 threads).
+template <bool F64SUM>
+__device__ __forceinline__ void rownorm4_block(const float *__restrict__ A, int64_t m, int64_t n,
+                                               int64_t lda, double *colnorm2, double *scal,
+                                               int *status, int bx, bool vec)
+{
+    __shared__ double wsum[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t row = (int64_t)bx * 8 + w;
+    double s = 0.0;
+    if (row < m) {
+        const float *a = A + row * lda;
+        bool finite = true;
+        const int64_t n4 = n >> 2;
+        for (int64_t q = lane; q < n4; q += 32) {
+            float4 v;
+            if (vec) {
+                v = reinterpret_cast<const float4 *>(a)[q];
+            } else {
+                v.x = a[4 * q];
+                v.y = a[4 * q + 1];
+                v.z = a[4 * q + 2];
+                v.w = a[4 * q + 3];
+            }
+            finite &= isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w);
+            if (F64SUM)
+                s += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+            else
+                s += (double)fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));
+        }
+        for (int64_t c = (n4 << 2) + lane; c < n; c += 32) {
+            const float v = a[c];
+            finite &= isfinite(v);
+            s += (double)v * (double)v;
+        }
+        if (!finite)
+            set_status(status, SVT_ERR_NONFINITE);
+        for (int o = 16; o > 0; o >>= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0)
+            colnorm2[row] = s;
+    }
+    if (lane == 0)
+        wsum[w] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int i = 0; i < 8; ++i)
+            b += wsum[i];
+        if (b != 0.0)
+            atomicAdd(&scal[SC_NRM_A2], b);
+    }
+}
+
+// Four consecutive values of row `row` from column `col` as BF16 (hi, and lo = the
+// rounding remainder when lo is non-null); one 8-byte store each where the four
+// elements are in range and 8-byte aligned.
+__device__ __forceinline__ void store4_bf16(void *hi, void *lo, int64_t row, int64_t col,
+                                            int64_t ld, int64_t ncols, bool aligned,
+                                            const float (&v)[4])
+{
+    __nv_bfloat16 h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        h[e] = __float2bfloat16_rn(v[e]);
+        l[e] = __float2bfloat16_rn(v[e] - __bfloat162float(h[e]));
+    }
+    const int64_t off = row * ld + col;
+    __nv_bfloat16 *ph = static_cast<__nv_bfloat16 *>(hi) + off;
+    __nv_bfloat16 *pl = lo ? static_cast<__nv_bfloat16 *>(lo) + off : nullptr;
+    if (aligned && col + 3 < ncols) {
+        uint2 uh, ul;
+        uh.x = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
+        uh.y = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
+        *reinterpret_cast<uint2 *>(ph) = uh;
+        if (pl) {
+            ul.x = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
+            ul.y = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
+            *reinterpret_cast<uint2 *>(pl) = ul;
+        }
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (col + e < ncols) {
+            ph[e] = h[e];
+            if (pl)
+                pl[e] = l[e];
+        }
+}
+
+__device__ __forceinline__ void store4_f64(void *out, int64_t row, int64_t col, int64_t ld,
+                                           int64_t ncols, const float (&v)[4])
+{
+    double *p = static_cast<double *>(out) + row * ld + col;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (col + e < ncols)
+            p[e] = (double)v[e];
+}
+
+// 64 x 64 tile (bx, by) of A -> same-orientation and transposed copies of A / alpha
+// (BF16 hi and optional lo parts, or FP64). 256 threads: thread t loads rows
+// (t >> 4) + 16 k, columns 4 (t & 15) .. + 3, and stores the transposed tile the same
+// way from shared memory. vec_in: A's rows 16-byte aligned; st_al: BF16 outputs
+// 8-byte aligned at columns that are multiples of 4.
+template <bool F64>
+__device__ __forceinline__ void split64_block(const float *__restrict__ A, int64_t m, int64_t n,
+                                              int64_t lda, float tau, void *xs_hi, void *xs_lo,
+                                              int64_t ld_s, void *xt_hi, void *xt_lo, int64_t ld_t,
+                                              double *scal, int bx, int by, bool vec_in, bool st_al)
+{
+    __shared__ float tile[64][65];
     const double nrm2 = scal[SC_NRM_A2];
     const double alpha = pow2_alpha(nrm2);
     const float inv_alpha = (float)(1.0 / alpha);  // exact power of two
-    if (bx == 0 && by == 0 && tx == 0 && ty == 0) {
+    if (bx == 0 && by == 0 && threadIdx.x == 0) {
         scal[SC_ALPHA] = alpha;
         scal[SC_INV_ALPHA2] = 1.0 / (alpha * alpha);
         scal[SC_TAU2_SCALED] = ((double)tau * (double)tau) / (alpha * alpha);
         scal[SC_NRM_X0] = nrm2 / (alpha * alpha);
     }
-    const int64_t i0 = (int64_t)by * 32, j0 = (int64_t)bx * 32;
-    for (int k = ty; k < 32; k += 8) {
-        const int64_t i = i0 + k, j = j0 + tx;
-        float x = (i < m && j < n) ? A[i * lda + j] * inv_alpha : 0.0f;
-        tile[k][tx] = x;
-        if (i < m && j < n && xs_hi) {
-            if (F64) {
-                static_cast<double *>(xs_hi)[i * ld_s + j] = (double)x;
-            } else {
-                __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                static_cast<__nv_bfloat16 *>(xs_hi)[i * ld_s + j] = hi;
-                if (xs_lo)
-                    static_cast<__nv_bfloat16 *>(xs_lo)[i * ld_s + j] =
-                        __float2bfloat16_rn(x - __bfloat162float(hi));
-            }
+    const int t = threadIdx.x, cq = t & 15, rr = t >> 4;
+    const int64_t i0 = (int64_t)by * 64, j0 = (int64_t)bx * 64;
+    const bool full_in = vec_in && i0 + 64 <= m && j0 + 64 <= n;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int li = rr + 16 * k;
+        const int64_t i = i0 + li, j = j0 + 4 * cq;
+        float v[4];
+        if (full_in) {
+            const float4 q = *reinterpret_cast<const float4 *>(A + i * lda + j);
+            v[0] = q.x;
+            v[1] = q.y;
+            v[2] = q.z;
+            v[3] = q.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                v[e] = (i < m && j + e < n) ? A[i * lda + j + e] : 0.0f;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            v[e] *= inv_alpha;
+            tile[li][4 * cq + e] = v[e];
+        }
+        if (xs_hi && i < m && j < n) {
+            if (F64)
+                store4_f64(xs_hi, i, j, ld_s, n, v);
+            else
+                store4_bf16(xs_hi, xs_lo, i, j, ld_s, n, st_al, v);
         }
     }
     __syncthreads();
-    for (int k = ty; k < 32; k += 8) {
-        const int64_t j = j0 + k, i = i0 + tx;  // transposed element (j, i)
-        if (i < m && j < n && xt_hi) {
-            float x = tile[tx][k];
-            if (F64) {
-                static_cast<double *>(xt_hi)[j * ld_t + i] = (double)x;
-            } else {
-                __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                static_cast<__nv_bfloat16 *>(xt_hi)[j * ld_t + i] = hi;
-                if (xt_lo)
-                    static_cast<__nv_bfloat16 *>(xt_lo)[j * ld_t + i] =
-                        __float2bfloat16_rn(x - __bfloat162float(hi));
-            }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int lj = rr + 16 * k;
+        const int64_t j = j0 + lj, i = i0 + 4 * cq;  // output row j, columns i .. i + 3
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            v[e] = tile[4 * cq + e][lj];
+        if (xt_hi && j < n && i < m) {
+            if (F64)
+                store4_f64(xt_hi, j, i, ld_t, m, v);
+            else
+                store4_bf16(xt_hi, xt_lo, j, i, ld_t, m, st_al, v);
         }
     }
 }
 
-template <bool F64>
-__global__ void ingest_split_kernel(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda,
-                                    float tau, void *xs_hi, void *xs_lo, int64_t ld_s, void *xt_hi,
-                                    void *xt_lo, int64_t ld_t, double *scal)
+__device__ __forceinline__ bool rows_vec(const float *A, int64_t lda)
 {
-    split_block<F64>(A, m, n, lda, tau, xs_hi, xs_lo, ld_s, xt_hi, xt_lo, ld_t, scal, blockIdx.x,
-                     blockIdx.y, threadIdx.x, threadIdx.y);
+    return (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && (lda & 3) == 0;
+}
+
+__device__ __forceinline__ bool bf16_outs_aligned(const void *a, const void *b, const void *c,
+                                                  const void *d, int64_t ld_s, int64_t ld_t)
+{
+    const uintptr_t u = reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
+                        reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(d);
+    return (u & 7u) == 0 && (ld_s & 3) == 0 && (ld_t & 3) == 0;
+}
+
+template <bool F64SUM>
+__global__ void __launch_bounds__(256) ingest_reduce_kernel(const float *__restrict__ A, int64_t m,
+                                                            int64_t n, int64_t lda, int wide,
+                                                            double *colnorm2, double *scal,
+                                                            int *status)
+{
+    const bool vec = rows_vec(A, lda);
+    if (!wide)
+        colnorm4_block<F64SUM>(A, m, n, lda, colnorm2, scal, status, blockIdx.x, blockIdx.y, vec);
+    else
+        rownorm4_block<F64SUM>(A, m, n, lda, colnorm2, scal, status, blockIdx.x, vec);
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(256) ingest_split_kernel(const float *__restrict__ A, int64_t m,
+                                                           int64_t n, int64_t lda, float tau,
+                                                           void *xs_hi, void *xs_lo, int64_t ld_s,
+                                                           void *xt_hi, void *xt_lo, int64_t ld_t,
+                                                           double *scal)
+{
+    split64_block<F64>(A, m, n, lda, tau, xs_hi, xs_lo, ld_s, xt_hi, xt_lo, ld_t, scal, blockIdx.x,
+                       blockIdx.y, rows_vec(A, lda),
+                       bf16_outs_aligned(xs_hi, xs_lo, xt_hi, xt_lo, ld_s, ld_t));
 }
 
 __global__ void finalize_kernel(double *scal, int *status, svt_status *user)
@@ -208,34 +369,46 @@ __global__ void grouped_zero_kernel(const AuxRec *recs)
         reinterpret_cast<unsigned long long *>(r.scal)[i] = 0ull;
 }
 
-__global__ void grouped_reduce_kernel(const AuxRec *recs, const CallRec *calls, int count)
+__global__ void __launch_bounds__(256) grouped_reduce_kernel(const AuxRec *recs,
+                                                             const CallRec *calls, int count)
 {
     const int i = find_rec(recs, count, blockIdx.x, false);
     const AuxRec &r = recs[i];
     const CallRec &c = calls[i];
     const int lb = blockIdx.x - r.blk_reduce;
+    const bool vec = rows_vec(c.A, c.lda);
     if (!r.wide) {
-        const int gx = (int)((r.n + 31) / 32);
-        colnorm_block(c.A, r.m, r.n, c.lda, r.colnorm, r.scal, r.status, lb % gx, lb / gx,
-                      threadIdx.x & 31, threadIdx.x >> 5);
+        const int gx = (int)((r.n + 127) / 128);
+        if (r.f64)
+            colnorm4_block<true>(c.A, r.m, r.n, c.lda, r.colnorm, r.scal, r.status, lb % gx,
+                                 lb / gx, vec);
+        else
+            colnorm4_block<false>(c.A, r.m, r.n, c.lda, r.colnorm, r.scal, r.status, lb % gx,
+                                  lb / gx, vec);
     } else {
-        rownorm_block(c.A, r.m, r.n, c.lda, r.colnorm, r.scal, r.status, lb, threadIdx.x);
+        if (r.f64)
+            rownorm4_block<true>(c.A, r.m, r.n, c.lda, r.colnorm, r.scal, r.status, lb, vec);
+        else
+            rownorm4_block<false>(c.A, r.m, r.n, c.lda, r.colnorm, r.scal, r.status, lb, vec);
     }
 }
 
-__global__ void grouped_split_kernel(const AuxRec *recs, const CallRec *calls, int count)
+__global__ void __launch_bounds__(256) grouped_split_kernel(const AuxRec *recs,
+                                                            const CallRec *calls, int count)
 {
     const int i = find_rec(recs, count, blockIdx.x, true);
     const AuxRec &r = recs[i];
     const CallRec &c = calls[i];
     const int lb = blockIdx.x - r.blk_split;
-    const int gx = (int)((r.n + 31) / 32);
+    const int gx = (int)((r.n + 63) / 64);
+    const bool vec = rows_vec(c.A, c.lda);
     if (r.f64)
-        split_block<true>(c.A, r.m, r.n, c.lda, c.tau, r.xs_hi, nullptr, r.ld_s, r.xt_hi, nullptr,
-                          r.ld_t, r.scal, lb % gx, lb / gx, threadIdx.x & 31, threadIdx.x >> 5);
+        split64_block<true>(c.A, r.m, r.n, c.lda, c.tau, r.xs_hi, nullptr, r.ld_s, r.xt_hi, nullptr,
+                            r.ld_t, r.scal, lb % gx, lb / gx, vec, false);
     else
-        split_block<false>(c.A, r.m, r.n, c.lda, c.tau, r.xs_hi, r.xs_lo, r.ld_s, r.xt_hi, r.xt_lo,
-                           r.ld_t, r.scal, lb % gx, lb / gx, threadIdx.x & 31, threadIdx.x >> 5);
+        split64_block<false>(c.A, r.m, r.n, c.lda, c.tau, r.xs_hi, r.xs_lo, r.ld_s, r.xt_hi,
+                             r.xt_lo, r.ld_t, r.scal, lb % gx, lb / gx, vec,
+                             bf16_outs_aligned(r.xs_hi, r.xs_lo, r.xt_hi, r.xt_lo, r.ld_s, r.ld_t));
 }
 
 __global__ void grouped_finalize_kernel(const AuxRec *recs, const CallRec *calls, int count)
@@ -359,15 +532,15 @@ __global__ void __launch_bounds__(256) f64_gemm_kernel(const __grid_constant__ F
 } // namespace
 
 cudaError_t ingest_reduce_launch(const float *A, int64_t m, int64_t n, int64_t lda, int wide,
-                                 double *colnorm2, double *scal, int *status, cudaStream_t s)
+                                 int f64, double *colnorm2, double *scal, int *status,
+                                 cudaStream_t s)
 {
-    if (!wide) {
-        dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + kRowsPerBlock - 1) / kRowsPerBlock));
-        ingest_colnorm_kernel<<<grid, dim3(32, 8), 0, s>>>(A, m, n, lda, colnorm2, scal, status);
-    } else {
-        unsigned blocks = (unsigned)((m + 7) / 8);
-        ingest_rownorm_kernel<<<blocks, 256, 0, s>>>(A, m, n, lda, colnorm2, scal, status);
-    }
+    dim3 grid = wide ? dim3((unsigned)((m + 7) / 8))
+                     : dim3((unsigned)((n + 127) / 128), (unsigned)((m + kColRows4 - 1) / kColRows4));
+    if (f64)
+        ingest_reduce_kernel<true><<<grid, 256, 0, s>>>(A, m, n, lda, wide, colnorm2, scal, status);
+    else
+        ingest_reduce_kernel<false><<<grid, 256, 0, s>>>(A, m, n, lda, wide, colnorm2, scal, status);
     return cudaGetLastError();
 }
 
@@ -377,24 +550,24 @@ cudaError_t ingest_split_launch(const float *A, int64_t m, int64_t n, int64_t ld
                                 cudaStream_t s)
 {
     (void)status;
-    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32));
+    dim3 grid((unsigned)((n + 63) / 64), (unsigned)((m + 63) / 64));
     if (f64)
-        ingest_split_kernel<true><<<grid, dim3(32, 8), 0, s>>>(A, m, n, lda, tau, xs_hi, nullptr,
-                                                                ld_s, xt_hi, nullptr, ld_t, scal);
+        ingest_split_kernel<true><<<grid, 256, 0, s>>>(A, m, n, lda, tau, xs_hi, nullptr, ld_s,
+                                                       xt_hi, nullptr, ld_t, scal);
     else
-        ingest_split_kernel<false><<<grid, dim3(32, 8), 0, s>>>(A, m, n, lda, tau, xs_hi, xs_lo,
-                                                                 ld_s, xt_hi, xt_lo, ld_t, scal);
+        ingest_split_kernel<false><<<grid, 256, 0, s>>>(A, m, n, lda, tau, xs_hi, xs_lo, ld_s,
+                                                        xt_hi, xt_lo, ld_t, scal);
     return cudaGetLastError();
 }
 
 int grouped_reduce_blocks(int64_t m, int64_t n, int wide)
 {
     if (!wide)
-        return (int)(((n + 31) / 32) * ((m + kRowsPerBlock - 1) / kRowsPerBlock));
+        return (int)(((n + 127) / 128) * ((m + kColRows4 - 1) / kColRows4));
     return (int)((m + 7) / 8);
 }
 
-int grouped_split_blocks(int64_t m, int64_t n) { return (int)(((n + 31) / 32) * ((m + 31) / 32)); }
+int grouped_split_blocks(int64_t m, int64_t n) { return (int)(((n + 63) / 64) * ((m + 63) / 64)); }
 
 cudaError_t grouped_zero_launch(const AuxRec *recs, int count, cudaStream_t s)
 {

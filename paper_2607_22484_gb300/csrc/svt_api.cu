@@ -760,7 +760,8 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
                 err = cudaMemsetAsync(base + L.strips, 0, L.strips_bytes, s);
             break;
         case OP_REDUCE:
-            err = ingest_reduce_launch(a.A, P.m, P.n, a.lda, P.wide ? 1 : 0, colnorm, scal, status, s);
+            err = ingest_reduce_launch(a.A, P.m, P.n, a.lda, P.wide ? 1 : 0, f64 ? 1 : 0, colnorm,
+                                       scal, status, s);
             break;
         case OP_SPLIT: {
             // same orientation as A: X (tall) when !wide, X^T when wide.

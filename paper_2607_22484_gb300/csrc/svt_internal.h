@@ -169,11 +169,13 @@ cudaError_t tc_gemm_launch_fused(const TcLaunch &l, int bn, int total_tiles, int
 constexpr int kEpiWarpsPublic = 8;  // completion count per tile of a fused launch
 cudaError_t f64_gemm_launch(const F64Launch &l, cudaStream_t s);
 
-// Ingest: FP64 column norms of the tall matrix and ||A||_F^2.
+// Ingest: column norms of the tall matrix and ||A||_F^2, summed in FP64 (squares in
+// FP32 over four values first unless f64, the FP64 tier).
 // wide = 0: tall matrix is A (M = m, N = n), colnorm2[j] = sum_i A[i][j]^2.
 // wide = 1: tall matrix is A^T (M = n, N = m), colnorm2[i] = sum_j A[i][j]^2.
 cudaError_t ingest_reduce_launch(const float *A, int64_t m, int64_t n, int64_t lda, int wide,
-                                 double *colnorm2, double *scal, int *status, cudaStream_t s);
+                                 int f64, double *colnorm2, double *scal, int *status,
+                                 cudaStream_t s);
 
 // Ingest: alpha = 2^round(log2 ||A||_F), X0 = A_tall / alpha written as
 //   xs (same orientation as A): hi (and lo when xs_lo), leading dim ld_s;
