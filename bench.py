@@ -176,6 +176,20 @@ def run_reference(args, n):
     return 0
 
 
+def replica_seed(rank):
+    """Seed of the matrix rank `rank` solves: every replica gets its own input."""
+    return 1002 + rank
+
+
+def job_throughput(local_ms, units_per_rank, world, reduce_max=None):
+    """Whole-job throughput of `world` replicas that each processed units_per_rank
+    units in local_ms of device time: the job's time is the slowest rank's
+    (reduce_max, a max-reduction over ranks, when world > 1) and the value counts the
+    units of all ranks. Returns (job_ms, units per second)."""
+    job_ms = float(reduce_max(local_ms)) if world > 1 else float(local_ms)
+    return job_ms, units_per_rank * world / (job_ms / 1e3)
+
+
 def config(n):
     return {"workload": workload_name(n), "m": n, "n": n, "tau": TAU, "iters": ITERS,
             "precision": "bf16", "schedule": "pe5", "polish": True,
@@ -496,7 +510,12 @@ def run_ours(args, n):
         if world > 1:
             dist.barrier()
 
-    A_np = wl.marchenko_pastur(n, seed=1002 + rank)
+    def max_over_ranks(v):
+        t = torch.tensor([v], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    A_np = wl.marchenko_pastur(n, seed=replica_seed(rank))
     A = torch.from_numpy(A_np).to(dev)
     Y = torch.empty_like(A)
     ctx = pkg.Context(local, workspace_bytes=pkg.workspace_bytes(n, n, iters=ITERS, prec="bf16"))
@@ -538,12 +557,7 @@ def run_ours(args, n):
     ctx.profile(False)
     launches = ctx.launch_count() - launches0
     st = int(status.item())
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = steps * world / (total_ms / 1e3)
+    total_ms, value = job_throughput(sum(step_ms), steps, world, max_over_ranks)
     if args.only_timed:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s",
@@ -567,12 +581,8 @@ def run_ours(args, n):
         ctx.polar_host(A_host, TAU, out_host=Y_host, **opts)
         e2e_ev[i][1].record()
     torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = e2e_steps * world / (e2e_ms / 1e3)
+    e2e_ms, e2e_value = job_throughput(sum(a.elapsed_time(b) for a, b in e2e_ev), e2e_steps,
+                                       world, max_over_ranks)
     finite = bool(torch.isfinite(Y_host).all().item())
 
     # The library's FP32-class tier and a plain PyTorch FP32 comparator (same schedule).
