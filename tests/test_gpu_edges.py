@@ -96,3 +96,57 @@ def test_argument_limits(ctx):
     with pytest.raises(pkg.SVTError) as e:
         ctx.polar(a, 0.1, ell0=1.5)
     assert e.value.status == pkg.binding.ERR_INVALID
+
+
+# --- the largest row count the API accepts: 2^20 x 1024 (and its transpose)
+#
+# 2^30 elements: the BF16 copies of X0 are 2 GiB and the FP32 input and output 4 GiB,
+# so every element offset and byte offset above 2^31 is exercised. The input has a
+# known SVD built from cheap exact pieces: U stacks 1024 blocks S_b Q / 32 (Q a random
+# 1024 x 1024 orthogonal matrix, S_b random sign diagonals), so U^T U = sum_b Q^T Q /
+# 1024 = I; A = U diag(sigma) V^T is then the stack of S_b B / 32 with
+# B = Q diag(sigma) V^T, and A_tau the stack of S_b B_tau / 32 with
+# B_tau = Q diag(max(sigma - tau, 0)) V^T (Eq. 1). Sign flips and the power-of-two
+# scale are exact, so B and B_tau (NumPy, FP64) fix every entry.
+
+def _stacked_known(seed):
+    rng = np.random.default_rng(seed)
+    n = 1024
+    sig = np.concatenate([rng.uniform(0.36, 1.0, 100), rng.uniform(0.0, 0.24, n - 100)])
+    sig[0] = 1.0
+    q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    v = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    b = (q * sig) @ v.T
+    b_tau = (q * np.maximum(sig - 0.3, 0.0)) @ v.T
+    signs = rng.choice(np.array([-1.0, 1.0], dtype=np.float32), size=(n, n))  # S_b diagonals
+    return b, b_tau, signs
+
+
+@pytest.mark.parametrize("wide", [False, True])
+def test_largest_row_count(ctx, wide):
+    nb, n = 1024, 1024
+    b, b_tau, signs = _stacked_known(31 + wide)
+    sgn = torch.from_numpy(signs).cuda()                      # (block, row) -> sign
+    blk = torch.from_numpy((b / 32.0).astype(np.float32)).cuda()
+    # A (tall): rows b * 1024 + i are signs[b, i] * B[i, :] / 32; the wide case is A^T.
+    a = (sgn[:, :, None] * blk[None, :, :]).reshape(nb * n, n)
+    if wide:
+        a = a.T.contiguous()
+    ctx.ensure_workspace(pkg.workspace_bytes(a.shape[0], a.shape[1], prec="bf16"))
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    y = ctx.polar(a, 0.3, status=st, iters=20, prec="bf16")
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    del a
+    if wide:
+        y = y.T
+    y = y.reshape(nb, n, n)
+    bt = torch.from_numpy(b_tau / 32.0).cuda()                # FP64
+    err2, ref2 = 0.0, 0.0
+    for k in range(0, nb, 128):  # FP64 error in slices of 128 blocks
+        e = y[k:k + 128].double() - sgn[k:k + 128, :, None].double() * bt[None]
+        err2 += float((e * e).sum())
+        ref2 += 128 * float((bt * bt).sum())
+    rel = (err2 / ref2) ** 0.5
+    print(f"{'1024 x 2^20' if wide else '2^20 x 1024'} BF16 relerr {rel:.3e}")
+    assert rel < 2e-2
