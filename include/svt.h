@@ -397,6 +397,35 @@ svt_status svt_autotune(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int
                         void *stream);
 
 /*
+ * svt_autotune_schedule: picks the iteration schedule -- polynomial steps per chain
+ * and ell0, the lower end of the first design interval of the Polar-Express-style
+ * schedule -- for a class of inputs represented by A, in the tier `opt` names. The
+ * paper leaves the iteration count open (maxIts: 11 in its code, 20 suggested, 25 in
+ * its timings); this measures the fewest steps that reach a given accuracy.
+ *   Reference: one FP32-tier solve of A with 32 steps and ell0 = 1e-3, into Yref.
+ *   Candidates: ell0 in {1e-3, 1e-2}; steps 2, 3, 4, 5, 6, 8, 10, 12, 14, 16, 20, 24,
+ *   28, 32 up to max_iters, in that order. For each ell0 the first step count whose
+ *   deviation ||Y - Yref||_F / ||Yref||_F (FP64 reduction; relative to ||A||_F when
+ *   Yref = 0) is <= target; the pick is the fewer steps (ties: ell0 = 1e-3). When no
+ *   candidate reaches the target: max_iters with ell0 = 1e-3.
+ *   opt: tier (BF16 or FP32) and the other options of the solves being tuned; its
+ *     iters, ell0 and schedule are the tuned quantities and are ignored (NULL =
+ *     defaults).
+ *   target: finite, > 0 (e.g. 2e-2 for the BF16 tier). max_iters: 2 .. 32.
+ *   Y, Yref: m x n FP32 device scratch (ldy, ldr >= n), overlapping neither A nor
+ *     each other; Y holds the last candidate's result on return.
+ *   Outputs: *iters_out, *ell0_out, and *dev_out, the pick's measured deviation.
+ * Synchronous: waits for each candidate on `stream`. Allocates 16 bytes of device
+ * memory for the reduction during the call (a tuning call, not a solve).
+ * Errors: as svt_polar_ex; SVT_ERR_INVALID also for target, max_iters, null outputs,
+ * overlapping buffers or the FP64 tier.
+ */
+svt_status svt_autotune_schedule(svt_ctx_t ctx, const float *A, int64_t m, int64_t n,
+                                 int64_t lda, float tau, const svt_options *opt, double target,
+                                 int max_iters, float *Y, int64_t ldy, float *Yref, int64_t ldr,
+                                 int *iters_out, double *ell0_out, double *dev_out, void *stream);
+
+/*
  * svt_polar_noalloc: the svt_polar_ex solve without any workspace from the
  * caller and without allocating device memory. (The paper has no counterpart:
  * this entry point exists for callers, not for the method.)

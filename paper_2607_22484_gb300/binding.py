@@ -40,7 +40,7 @@ EXPORTS = [
     "svt_ctx_sync", "svt_schedule_coeffs", "svt_debug_gemm_bf16", "svt_debug_gemm_bf16_ex",
     "svt_ctx_launch_count",
     "svt_ctx_profile", "svt_ctx_profile_read", "svt_polar_noalloc", "svt_autotune",
-    "svt_prox_grad_step", "svt_complete",
+    "svt_prox_grad_step", "svt_complete", "svt_autotune_schedule",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -135,6 +135,11 @@ def lib():
         L.svt_complete.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, i64, i64,
                                    ctypes.POINTER(CompletionParams), ctypes.POINTER(Options), vp,
                                    vp]
+        L.svt_autotune_schedule.argtypes = [vp, vp, i64, i64, i64, ctypes.c_float,
+                                            ctypes.POINTER(Options), ctypes.c_double, i32, vp,
+                                            i64, vp, i64, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double), vp]
         L.svt_ctx_launch_count.argtypes = [vp]
         L.svt_ctx_launch_count.restype = ctypes.c_uint64
         L.svt_ctx_profile.argtypes = [vp, i32]
@@ -375,6 +380,30 @@ class Context:
                                   ctypes.c_void_p(stats.data_ptr()),
                                   ctypes.c_void_p(_stream_ptr(stream))), "svt_complete")
         return X, stats
+
+    def autotune_schedule(self, A, tau: float, target: float, max_iters: int = 32, stream=None,
+                          **opts):
+        """The fewest polynomial steps (and ell0) whose solve of A stays within `target` of
+        an FP32-tier 32-step reference (svt_autotune_schedule). Returns
+        {"iters", "ell0", "deviation"}."""
+        import torch
+        a_ptr, m, n, lda = _f32_matrix(A, "A")
+        Y = torch.empty((m, n), dtype=torch.float32, device=A.device)
+        R = torch.empty((m, n), dtype=torch.float32, device=A.device)
+        o = make_options(**opts)
+        ref, cand = dict(opts), dict(opts)
+        ref.update(prec="fp32", iters=32)
+        cand.update(iters=int(max_iters))
+        self.ensure_workspace(max(workspace_bytes(m, n, **ref), workspace_bytes(m, n, **cand)))
+        k, l0, dev = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().svt_autotune_schedule(self.handle, ctypes.c_void_p(a_ptr), m, n, lda,
+                                           ctypes.c_float(tau), ctypes.byref(o), float(target),
+                                           int(max_iters), ctypes.c_void_p(Y.data_ptr()), n,
+                                           ctypes.c_void_p(R.data_ptr()), n, ctypes.byref(k),
+                                           ctypes.byref(l0), ctypes.byref(dev),
+                                           ctypes.c_void_p(_stream_ptr(stream))),
+               "svt_autotune_schedule")
+        return {"iters": k.value, "ell0": l0.value, "deviation": dev.value}
 
     def autotune(self, A, tau: float, out=None, reps: int = 2, stream=None, **opts):
         """Pick the product kernel's tile width per launch for this shape and options

@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "libsvt.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["gemm_tc.cu", "aux_kernels.cu", "svt_api.cu", "serve.cpp", "schedule.cpp", "noalloc.cu",
-           "completion.cu"]
+           "completion.cu", "autotune_schedule.cu"]
 
 
 def _nvcc() -> str:

@@ -171,6 +171,40 @@ def test_autotuned_plan_matches_oracle(ctx):
     assert oracle.relerr(y.cpu().numpy(), exact) < 2e-2
 
 
+@pytest.mark.parametrize("prec,target", [("bf16", 2e-2), ("fp32", 1e-4)])
+def test_schedule_autotune_meets_its_target(ctx, prec, target):
+    """svt_autotune_schedule picks the fewest steps (and ell0) within `target` of an
+    FP32-tier 32-step reference. With a 6 % gap that reference is exact to ~1e-6, so the
+    pick's error against Eq. 1 is its reported deviation up to that, and within the
+    target."""
+    a = _gap_matrix(520, 384, seed=23)
+    exact = oracle.svt_definition(a.astype(np.float64), 0.3)
+    dev = torch.from_numpy(a).cuda()
+    pick = ctx.autotune_schedule(dev, 0.3, target, prec=prec)
+    print(f"{prec}: {pick}")
+    assert 2 <= pick["iters"] <= 32 and pick["ell0"] in (1e-3, 1e-2)
+    assert pick["deviation"] <= target
+    y, st = _run(ctx, a, 0.3, iters=pick["iters"], ell0=pick["ell0"], schedule="pe5", prec=prec)
+    assert st == 0
+    err = oracle.relerr(y, exact)
+    assert err <= target + 1e-5, (err, pick)
+    assert abs(err - pick["deviation"]) <= 0.05 * target + 1e-5, (err, pick)
+    # the BF16 tier needs fewer steps for 2e-2 than the FP32 tier for 1e-4, and some
+    if prec == "bf16":
+        assert pick["iters"] <= 12
+
+
+def test_schedule_autotune_unreachable_target_and_errors(ctx):
+    a = _gap_matrix(200, 130, seed=24)
+    dev = torch.from_numpy(a).cuda()
+    pick = ctx.autotune_schedule(dev, 0.3, 1e-9, max_iters=6, prec="bf16")
+    assert pick["iters"] == 6 and pick["ell0"] == 1e-3 and pick["deviation"] > 1e-9
+    for kw in ({"target": 0.0}, {"target": float("nan")}, {"target": 1e-2, "max_iters": 1},
+               {"target": 1e-2, "max_iters": 33}, {"target": 1e-2, "prec": "fp64"}):
+        with pytest.raises(pkg.SVTError):
+            ctx.autotune_schedule(dev, 0.3, **kw)
+
+
 @pytest.mark.parametrize("prec,shape", [("bf16", (520, 384)), ("fp32", (300, 700)), ("bf16", (1024, 1024))])
 def test_fused_launch_matches_separate_launches(ctx, prec, shape):
     """All products in one persistent launch with device-side dependencies give the
