@@ -254,8 +254,30 @@ def batch_extra(ctx_cls, pkg, torch, dev, steps=5, warmup=2):
     torch.cuda.synchronize()
     ms1 = e0.elapsed_time(e1)
     fl = sum(alg_flops(it.m, it.n, ITERS) for it in items)
+    # The same batch with the iteration schedule svt_autotune_schedule picks (target 2e-2)
+    # on eight of its matrices: the pick needing the most steps serves the whole batch.
+    tuner = ctx_cls(dev.index or 0, workspace_bytes=1 << 20)
+    picks = [tuner.autotune_schedule(As[i], taus[i], 2e-2, prec="bf16")
+             for i in range(0, len(items), len(items) // 8)]
+    pick = max(picks, key=lambda p: (p["iters"], -p["ell0"]))
+    topts = {"iters": pick["iters"], "ell0": pick["ell0"], "schedule": "pe5", "prec": "bf16"}
+    for _ in range(warmup):
+        ctx.batch(As, taus, outs=outs, opts=topts)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        ctx.batch(As, taus, outs=outs, opts=topts)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_t = e0.elapsed_time(e1) / steps
     return {"workload": "256 low-rank+noise matrices, size log-uniform 128-1024, aspect {1,2,1/2}, "
                         "rank 5-50, tau = noise edge + 0.5, BF16 tier, 20 steps",
+            "autotuned_schedule": {"iters": pick["iters"], "ell0": pick["ell0"],
+                                   "max_deviation_at_sample_picks":
+                                       max(p["deviation"] for p in picks),
+                                   "samples": len(picks),
+                                   "solves_per_s": len(items) / (ms_t / 1e3),
+                                   "ms_per_batch": ms_t},
             "solves_per_s": len(items) / (ms / 1e3), "ms_per_batch": ms,
             "alg_tflops": fl / (ms / 1e3) / 1e12,
             "one_at_a_time_solves_per_s": len(items) / (ms1 / 1e3),
@@ -420,6 +442,33 @@ def svd_context(torch, A, tau, reps=2):
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
+
+
+def paper_shapes_extra(ctx_cls, pkg, torch, dev, reps=5):
+    """The one number the paper reports (Section 3, Fig. 2): about 10x over SVD-based
+    SVT (torch.linalg.svd), on m x (m + 1) iid Gaussian inputs, m = 1000 ... 5000, 25
+    Polar-Express iterations in bfloat16, three unnamed Colab GPUs. Same shapes and
+    iteration count here (entries N(0, 1/(m + 1)), sigma in ~[0, 2]; tau = 1), BF16
+    tier, against torch.linalg.svd SVT on this GPU."""
+    import svt_workloads as wl
+    out = {"paper": "about 10x over torch.linalg.svd SVT (three unnamed Colab GPUs)"}
+    ctx = ctx_cls(dev.index or 0, workspace_bytes=1 << 20)
+    for m in (1000, 3000, 5000):
+        A = torch.from_numpy(wl.marchenko_pastur(m, m + 1, seed=1010 + m)).to(dev)
+        Y = torch.empty_like(A)
+        opts = {"iters": 25, "prec": "bf16"}
+        ctx.polar(A, 1.0, out=Y, **opts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        for _ in range(reps):
+            ctx.polar(A, 1.0, out=Y, **opts)
+        e1.record()
+        torch.cuda.synchronize()
+        ours = e0.elapsed_time(e1) / reps
+        svd = svd_context(torch, A, 1.0, reps=1)
+        out[f"{m}x{m + 1}"] = {"ms": ours, "torch_svd_ms": svd, "speedup_vs_torch_svd": svd / ours}
+    return out
 
 
 def serving_extra(ctx_cls, pkg, torch, dev, n_req=200):
@@ -678,6 +727,7 @@ def run_ours(args, n):
         line["shapes"] = shapes_extra(pkg.Context, pkg, torch, dev)
         line["vs_fp32"]["torch_linalg_svd_svt_ms"] = svd_context(torch, A, TAU)
         line["schedule_autotune"] = schedule_extra(ctx, torch, A)
+        line["paper_shapes"] = paper_shapes_extra(pkg.Context, pkg, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
         est, desc, cores = oracle_sample(n, 1002, 96, repeats=1)
         line["cpu_baseline"] = {"value": 1.0 / est[0], "unit": "solves/s", "cores": cores,
