@@ -64,8 +64,13 @@ typedef enum {
     SVT_FP64 = 0, /* every step in FP64 (SIMT); correctness tier, small inputs */
     SVT_FP32 = 1, /* every product FP32-class: three BF16 tensor-core products
                      (hi*hi + hi*lo + lo*hi) with FP32 accumulation */
-    SVT_BF16 = 2  /* polynomial steps in BF16 (FP32 accumulation); Gram, polish
+    SVT_BF16 = 2, /* polynomial steps in BF16 (FP32 accumulation); Gram, polish
                      and combine FP32-class; norms and the tau^2 shift in FP64 */
+    SVT_FP8_EXPERIMENTAL = 3 /* reserved, not built: every entry point returns
+                     SVT_ERR_UNSUPPORTED. Block-scaled e4m3 operands in even the
+                     first two polynomial steps put the relative error near 20 %,
+                     ten times the BF16 tier's 2e-2: later steps converge to the
+                     polar factor of the rounded iterate, they do not undo it */
 } svt_precision;
 
 typedef enum {

@@ -22,8 +22,8 @@ LIB_PATH = os.path.join(_HERE, "libsvt.so")
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_DIVERGED, ERR_TIMEOUT, \
     ERR_NOT_READY, ERR_BUSY, ERR_UNSUPPORTED = range(10)
 # svt_precision
-FP64, FP32, BF16 = 0, 1, 2
-PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
+FP64, FP32, BF16, FP8_EXPERIMENTAL = 0, 1, 2, 3
+PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp8_experimental": FP8_EXPERIMENTAL}
 # svt_schedule_kind / svt_norm_kind / svt_mode
 SCHED_AUTO, SCHED_PE5, SCHED_NS3 = 0, 1, 2
 SCHED = {"auto": SCHED_AUTO, "pe5": SCHED_PE5, "ns3": SCHED_NS3}

@@ -81,7 +81,9 @@ extern "C" svt_status svt_autotune_schedule(svt_ctx_t ctx, const float *A, int64
     if (opt)
         base = *opt;
     Resolved r;
-    if (!resolve(&base, &r) || r.prec == SVT_FP64)
+    if ((st = resolve_status(&base, &r)) != SVT_OK)
+        return st;
+    if (r.prec == SVT_FP64)
         return SVT_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaSetDevice(ctx->device) != cudaSuccess)

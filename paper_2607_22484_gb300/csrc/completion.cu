@@ -211,9 +211,10 @@ extern "C" svt_status svt_prox_grad_step(svt_ctx_t ctx, float *X, int64_t ldx, c
         return SVT_ERR_INVALID;
     // Everything the solve checks (sizes, options, workspace) before any launch.
     svt::Resolved r;
-    if (!svt::resolve(opt, &r))
-        return SVT_ERR_INVALID;
-    svt_status st = svt::validate(Z, m, n, ldz, step * lambda, X, ldx);
+    svt_status st = svt::resolve_status(opt, &r);
+    if (st != SVT_OK)
+        return st;
+    st = svt::validate(Z, m, n, ldz, step * lambda, X, ldx);
     if (st != SVT_OK)
         return st;
     if (r.prec == SVT_FP64 && (m > svt::kF64MaxDim || n > svt::kF64MaxDim))
@@ -451,9 +452,10 @@ extern "C" svt_status svt_complete(svt_ctx_t ctx, float *X, int64_t ldx, const f
             if (overlaps(spans[i].p, spans[i].b, spans[j].p, spans[j].b))
                 return SVT_ERR_INVALID;
     Resolved r;
-    if (!resolve(opt, &r))
-        return SVT_ERR_INVALID;
-    svt_status st = validate(Z, m, n, ldz, q.step * q.lambda0, X, ldx);
+    svt_status st = resolve_status(opt, &r);
+    if (st != SVT_OK)
+        return st;
+    st = validate(Z, m, n, ldz, q.step * q.lambda0, X, ldx);
     if (st != SVT_OK)
         return st;
     if (r.prec == SVT_FP64 && (m > kF64MaxDim || n > kF64MaxDim))

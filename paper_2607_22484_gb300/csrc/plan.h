@@ -39,6 +39,9 @@ struct Resolved {
 };
 
 bool resolve(const svt_options *in, Resolved *r);
+// resolve() as a status: SVT_ERR_UNSUPPORTED for the reserved FP8 tier, SVT_ERR_INVALID
+// for any other option outside its range.
+svt_status resolve_status(const svt_options *in, Resolved *r);
 
 // A matrix buffer in the workspace: hi part and (FP32-class pairs) lo part.
 struct Buf {

@@ -957,14 +957,14 @@ int batch_bn(const svt_matrix *mats, int count)
     return a128 < a256 ? 128 : 256;
 }
 
-// Options of all matrices resolved; returns false on an invalid option set.
-bool resolve_all(const svt_matrix *mats, int count, std::vector<Resolved> &res, bool *same)
+// Options of all matrices resolved: SVT_OK, or the first matrix's option status.
+svt_status resolve_all(const svt_matrix *mats, int count, std::vector<Resolved> &res, bool *same)
 {
     res.resize(count);
     *same = true;
     for (int i = 0; i < count; ++i) {
-        if (!resolve(&mats[i].opt, &res[i]))
-            return false;
+        if (svt_status st = resolve_status(&mats[i].opt, &res[i]))
+            return st;
         if (i > 0 && !same_options(res[i], res[0]))
             *same = false;
     }
@@ -972,7 +972,7 @@ bool resolve_all(const svt_matrix *mats, int count, std::vector<Resolved> &res, 
         *same = false;  // the FP64 tier runs per-matrix launches
     if (count > 0 && (!res[0].polish || res[0].mode != SVT_MODE_SVT))
         *same = false;  // grouped kernels cover the default pipeline
-    return true;
+    return SVT_OK;
 }
 
 } // namespace
@@ -985,8 +985,8 @@ svt_status svt_batch_workspace_bytes(const svt_matrix *mats, int count, size_t *
         return SVT_ERR_INVALID;
     std::vector<Resolved> res;
     bool same = false;
-    if (!resolve_all(mats, count, res, &same))
-        return SVT_ERR_INVALID;
+    if (svt_status rs = resolve_all(mats, count, res, &same))
+        return rs;
     size_t total = 0;
     for (int i = 0; i < count; ++i) {
         if (mats[i].m <= 0 || mats[i].n <= 0)
@@ -1009,8 +1009,8 @@ svt_status svt_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, void *str
         return SVT_ERR_BUSY;
     std::vector<Resolved> res;
     bool same = false;
-    if (!resolve_all(mats, count, res, &same))
-        return SVT_ERR_INVALID;
+    if (svt_status rs = resolve_all(mats, count, res, &same))
+        return rs;
     size_t total = 0;
     std::vector<size_t> off(count);
     for (int i = 0; i < count; ++i) {
@@ -1119,8 +1119,8 @@ svt_status svt_serve_submit(svt_ctx_t ctx, const svt_matrix *req, uint64_t *tick
     if (st != SVT_OK)
         return st;
     Resolved r;
-    if (!resolve(&req->opt, &r))
-        return SVT_ERR_INVALID;
+    if ((st = resolve_status(&req->opt, &r)) != SVT_OK)
+        return st;
     if (r.prec == SVT_FP64 && (req->m > kF64MaxDim || req->n > kF64MaxDim))
         return SVT_ERR_UNSUPPORTED;
     // Large requests: one fused solve; small ones: per-stage problems grouped in windows.

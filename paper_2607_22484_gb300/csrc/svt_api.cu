@@ -117,6 +117,13 @@ void attach_store_maps(TcProblem &p)
 }
 
 
+svt_status resolve_status(const svt_options *in, Resolved *r)
+{
+    if (in && in->prec == SVT_FP8_EXPERIMENTAL)
+        return SVT_ERR_UNSUPPORTED;
+    return resolve(in, r) ? SVT_OK : SVT_ERR_INVALID;
+}
+
 bool resolve(const svt_options *in, Resolved *r)
 {
     svt_options o;
@@ -1146,8 +1153,10 @@ void svt_options_default(svt_options *o)
 svt_status svt_workspace_bytes_ex(int64_t m, int64_t n, const svt_options *opt, size_t *out)
 {
     Resolved r;
-    if (!out || m <= 0 || n <= 0 || !resolve(opt, &r))
+    if (!out || m <= 0 || n <= 0)
         return SVT_ERR_INVALID;
+    if (svt_status rs = resolve_status(opt, &r))
+        return rs;
     *out = make_layout(m, n, r).total;
     return SVT_OK;
 }
@@ -1215,8 +1224,8 @@ svt_status svt_polar_ex(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int
     if (st != SVT_OK)
         return st;
     Resolved r;
-    if (!resolve(opt, &r))
-        return SVT_ERR_INVALID;
+    if ((st = resolve_status(opt, &r)) != SVT_OK)
+        return st;
     if (r.prec == SVT_FP64 && (m > kF64MaxDim || n > kF64MaxDim))
         return SVT_ERR_UNSUPPORTED;
     if (serve_busy(ctx))
@@ -1242,8 +1251,10 @@ svt_status svt_autotune(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int
     if (st != SVT_OK)
         return st;
     Resolved r;
-    if (!resolve(opt, &r) || reps < 1)
+    if (reps < 1)
         return SVT_ERR_INVALID;
+    if ((st = resolve_status(opt, &r)) != SVT_OK)
+        return st;
     if (r.prec == SVT_FP64)
         return SVT_OK;  // the FP64 tier has no tile choice
     if (serve_busy(ctx))

@@ -45,6 +45,16 @@ def test_workspace_bytes():
         pkg.workspace_bytes(0, 5)
 
 
+def test_reserved_fp8_tier_is_unsupported():
+    """SVT_FP8_EXPERIMENTAL is reserved: rejected as unsupported, not as invalid."""
+    with pytest.raises(pkg.SVTError) as e:
+        pkg.workspace_bytes(64, 64, prec="fp8_experimental")
+    assert e.value.status == pkg.binding.ERR_UNSUPPORTED
+    with pytest.raises(pkg.SVTError) as e:
+        pkg.workspace_bytes(64, 64, prec=7)
+    assert e.value.status == pkg.binding.ERR_INVALID
+
+
 @pytest.mark.parametrize("delta", [0.0, 0.01, 1e-4])
 @pytest.mark.parametrize("ell0", [1e-3, 1e-2])
 def test_schedule_matches_oracle(delta, ell0):
