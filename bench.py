@@ -254,13 +254,16 @@ def batch_extra(ctx_cls, pkg, torch, dev, steps=5, warmup=2):
     torch.cuda.synchronize()
     ms1 = e0.elapsed_time(e1)
     fl = sum(alg_flops(it.m, it.n, ITERS) for it in items)
+    # Tile width measured for this batch (svt_autotune_batch) against the cost model's.
+    tile, ms_tile = ctx.autotune_batch(As, taus, outs=outs, reps=steps, opts=opts)
     # The same batch with the iteration schedule svt_autotune_schedule picks (target 2e-2)
     # on eight of its matrices: the pick needing the most steps serves the whole batch.
     tuner = ctx_cls(dev.index or 0, workspace_bytes=1 << 20)
     picks = [tuner.autotune_schedule(As[i], taus[i], 2e-2, prec="bf16")
              for i in range(0, len(items), len(items) // 8)]
     pick = max(picks, key=lambda p: (p["iters"], -p["ell0"]))
-    topts = {"iters": pick["iters"], "ell0": pick["ell0"], "schedule": "pe5", "prec": "bf16"}
+    topts = {"iters": pick["iters"], "ell0": pick["ell0"], "schedule": "pe5", "prec": "bf16",
+             "tile": tile}
     for _ in range(warmup):
         ctx.batch(As, taus, outs=outs, opts=topts)
     torch.cuda.synchronize()
@@ -272,7 +275,10 @@ def batch_extra(ctx_cls, pkg, torch, dev, steps=5, warmup=2):
     ms_t = e0.elapsed_time(e1) / steps
     return {"workload": "256 low-rank+noise matrices, size log-uniform 128-1024, aspect {1,2,1/2}, "
                         "rank 5-50, tau = noise edge + 0.5, BF16 tier, 20 steps",
-            "autotuned_schedule": {"iters": pick["iters"], "ell0": pick["ell0"],
+            "tile_autotune": {"tile": tile, "ms_per_batch": ms_tile,
+                              "solves_per_s": len(items) / (ms_tile / 1e3),
+                              "cost_model_ms_per_batch": ms},
+            "autotuned_schedule": {"iters": pick["iters"], "ell0": pick["ell0"], "tile": tile,
                                    "max_deviation_at_sample_picks":
                                        max(p["deviation"] for p in picks),
                                    "samples": len(picks),

@@ -123,8 +123,11 @@ typedef struct {
                                    CTA per 128 x 128 or 128 x 256 tile; 512 = a
                                    cluster of two CTAs per 256 x 256 tile
                                    (tcgen05 cta_group::2, each CTA staging half of
-                                   the tile's operands). Batches and serving choose
-                                   their own tiles. Other values: SVT_ERR_INVALID */
+                                   the tile's operands). A grouped batch takes 128
+                                   or 256 from its matrices' options (0 or 512:
+                                   chosen by a cost model, see svt_autotune_batch);
+                                   serving chooses its own tiles. Other values:
+                                   SVT_ERR_INVALID */
 } svt_options;
 
 typedef struct svt_ctx *svt_ctx_t;
@@ -429,6 +432,17 @@ svt_status svt_autotune_schedule(svt_ctx_t ctx, const float *A, int64_t m, int64
                                  int64_t lda, float tau, const svt_options *opt, double target,
                                  int max_iters, float *Y, int64_t ldy, float *Yref, int64_t ldr,
                                  int *iters_out, double *ell0_out, double *dev_out, void *stream);
+
+/*
+ * svt_autotune_batch: times the grouped batch `mats` with 128- and 256-wide product
+ * tiles (one untimed call each, then `reps` timed svt_batch calls on `stream`) and
+ * returns the faster width in *tile_out (and its mean time per batch in *ms_out,
+ * nullable). Set svt_options.tile of the batch's matrices to it. The outputs of
+ * `mats` are written by every call. Synchronous. Errors: as svt_batch;
+ * SVT_ERR_INVALID for count <= 0, reps < 1 or a null tile_out.
+ */
+svt_status svt_autotune_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, int reps,
+                              void *stream, int *tile_out, double *ms_out);
 
 /*
  * svt_polar_noalloc: the svt_polar_ex solve without any workspace from the

@@ -40,7 +40,7 @@ EXPORTS = [
     "svt_ctx_sync", "svt_schedule_coeffs", "svt_debug_gemm_bf16", "svt_debug_gemm_bf16_ex",
     "svt_ctx_launch_count",
     "svt_ctx_profile", "svt_ctx_profile_read", "svt_polar_noalloc", "svt_autotune",
-    "svt_prox_grad_step", "svt_complete", "svt_autotune_schedule",
+    "svt_prox_grad_step", "svt_complete", "svt_autotune_schedule", "svt_autotune_batch",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -140,6 +140,9 @@ def lib():
                                             i64, vp, i64, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double), vp]
+        L.svt_autotune_batch.argtypes = [vp, ctypes.POINTER(Matrix), i32, i32, vp,
+                                         ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_double)]
         L.svt_ctx_launch_count.argtypes = [vp]
         L.svt_ctx_launch_count.restype = ctypes.c_uint64
         L.svt_ctx_profile.argtypes = [vp, i32]
@@ -505,6 +508,30 @@ class Context:
         _check(lib().svt_batch(self.handle, arr, count, ctypes.c_void_p(_stream_ptr(stream))),
                "svt_batch")
         return outs
+
+    def autotune_batch(self, As, taus, outs=None, reps: int = 3, stream=None, opts=None):
+        """svt_autotune_batch: the faster product tile width (128 or 256) of this grouped
+        batch, from timed runs. Returns (tile, ms per batch); pass opts tile=<tile> to
+        later batch() calls."""
+        import torch
+        count = len(As)
+        if outs is None:
+            outs = [torch.empty_like(a) for a in As]
+        opts = opts or [{}] * count
+        if isinstance(opts, dict):
+            opts = [opts] * count
+        arr = (Matrix * count)()
+        for i in range(count):
+            arr[i] = self._matrix(As[i], taus[i], outs[i], None, opts[i])
+        need = ctypes.c_size_t(0)
+        _check(lib().svt_batch_workspace_bytes(arr, count, ctypes.byref(need)),
+               "svt_batch_workspace_bytes")
+        self.ensure_workspace(int(need.value))
+        tile, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(lib().svt_autotune_batch(self.handle, arr, count, int(reps),
+                                        ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(tile),
+                                        ctypes.byref(ms)), "svt_autotune_batch")
+        return tile.value, ms.value
 
     def submit(self, A, tau, out, status=None, **opts) -> int:
         """Queue one serving request (svt_serve_submit); returns its ticket."""

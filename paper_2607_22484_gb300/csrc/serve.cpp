@@ -183,6 +183,7 @@ struct BatchPlan {
 struct BatchKey {
     std::vector<int64_t> shapes;     // m0, n0, m1, n1, ...
     Resolved r;
+    int bn = 0;                      // product tile width of the grouped launch
     bool operator<(const BatchKey &o) const
     {
         auto tie_r = [](const Resolved &x) {
@@ -191,6 +192,8 @@ struct BatchKey {
         };
         if (shapes != o.shapes)
             return shapes < o.shapes;
+        if (bn != o.bn)
+            return bn < o.bn;
         return tie_r(r) < tie_r(o.r);
     }
 };
@@ -1035,6 +1038,7 @@ svt_status svt_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, void *str
     if (same && total + batch_table_bytes(count, res[0]) <= ctx->ws_bytes) {
         BatchKey key;
         key.r = res[0];
+        key.bn = (res[0].tile == 128 || res[0].tile == 256) ? res[0].tile : batch_bn(mats, count);
         for (int i = 0; i < count; ++i) {
             key.shapes.push_back(mats[i].m);
             key.shapes.push_back(mats[i].n);
@@ -1047,8 +1051,7 @@ svt_status svt_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, void *str
             if (s->batches.size() > 16)
                 s->batches.clear();
             auto nb = std::make_unique<BatchPlan>();
-            svt_status st = build_batch(ctx, s, mats, count, res[0], off, total, batch_bn(mats, count),
-                                        nb.get());
+            svt_status st = build_batch(ctx, s, mats, count, res[0], off, total, key.bn, nb.get());
             if (st == SVT_OK) {
                 bp = nb.get();
                 s->batches[key] = std::move(nb);
@@ -1108,6 +1111,58 @@ svt_status svt_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, void *str
             cudaStreamWaitEvent(cs, s->events[1 + i], 0) != cudaSuccess)
             return SVT_ERR_CUDA;
     }
+    return SVT_OK;
+}
+
+svt_status svt_autotune_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, int reps,
+                              void *stream, int *tile_out, double *ms_out)
+{
+    if (!ctx || !mats || count <= 0 || reps < 1 || !tile_out)
+        return SVT_ERR_INVALID;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    std::vector<svt_matrix> m(mats, mats + count);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0)
+            cudaEventDestroy(e0);
+        return SVT_ERR_CUDA;
+    }
+    svt_status st = SVT_OK;
+    int best = 0;
+    float best_ms = 0.0f;
+    for (int bn : {128, 256}) {
+        for (svt_matrix &x : m)
+            x.opt.tile = bn;
+        // one untimed call builds and records the batch's launches
+        if ((st = svt_batch(ctx, m.data(), count, stream)) != SVT_OK)
+            break;
+        if (cudaEventRecord(e0, cs) != cudaSuccess) {
+            st = SVT_ERR_CUDA;
+            break;
+        }
+        for (int r = 0; r < reps && st == SVT_OK; ++r)
+            st = svt_batch(ctx, m.data(), count, stream);
+        float ms = 0.0f;
+        if (st != SVT_OK || cudaEventRecord(e1, cs) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            if (st == SVT_OK)
+                st = SVT_ERR_CUDA;
+            break;
+        }
+        ms /= (float)reps;
+        if (!best || ms < best_ms) {
+            best = bn;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SVT_OK)
+        return st;
+    *tile_out = best;
+    if (ms_out)
+        *ms_out = best_ms;
     return SVT_OK;
 }
 

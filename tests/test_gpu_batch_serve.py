@@ -40,6 +40,25 @@ def test_batch_matches_oracle_and_single():
             assert oracle.relerr(got, exact) < 2e-2, (it.m, it.n)
 
 
+def test_batch_tile_option_and_autotune():
+    """A grouped batch takes its product tile width from the matrices' options (128 or
+    256); both widths give the single-solve results, and svt_autotune_batch picks one."""
+    items = _items(8)
+    ctx = pkg.Context(0, workspace_bytes=1 << 20)
+    As = [torch.from_numpy(it.matrix()).cuda() for it in items]
+    taus = [it.tau for it in items]
+    single = pkg.Context(0, workspace_bytes=1 << 20)
+    refs = [single.polar(a, t, iters=20, prec="bf16") for a, t in zip(As, taus)]
+    for tile in (128, 256):
+        outs = ctx.batch(As, taus, opts={"iters": 20, "prec": "bf16", "tile": tile})
+        torch.cuda.synchronize()
+        for y, r in zip(outs, refs):
+            assert oracle.relerr(y.cpu().numpy().astype(np.float64),
+                                 r.cpu().numpy().astype(np.float64)) < 1e-5, tile
+    tile, ms = ctx.autotune_batch(As, taus, reps=2, opts={"iters": 20, "prec": "bf16"})
+    assert tile in (128, 256) and ms > 0.0
+
+
 def _serve(ctx, items, tiers, statuses=None):
     # Inputs are made before the first submission: generating them in between would
     # compete for the host cores with the serving thread.
