@@ -370,10 +370,25 @@ def completion_extra(ctx_cls, pkg, torch, dev, steps=100, svd_steps=10):
                              "ms_per_step": e0.elapsed_time(e1) / max(1, info["steps"]),
                              "recovery": rec(X), **{k: v for k, v in kw.items() if k != "lam0"}}
     device_loop["continuation"]["lambda0_over_lambda"] = 25.0
+    # The same 100 steps with the schedule svt_autotune_schedule picks (target 2e-2) on
+    # the first step's input, P_Omega(M), at tau = lambda.
+    pick = ctx.autotune_schedule(M * Wf, lam, 2e-2, prec="bf16")
+    sopts = {"iters": pick["iters"], "ell0": pick["ell0"], "schedule": "pe5", "prec": "bf16"}
+    X.zero_()
+    ctx.prox_grad_step(X, M, W, lam, Z=Z, **sopts)
+    X.zero_()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        ctx.prox_grad_step(X, M, W, lam, Z=Z, **sopts)
+    e1.record()
+    torch.cuda.synchronize()
+    tuned = {"iters": pick["iters"], "ell0": pick["ell0"], "deviation": pick["deviation"],
+             "ms_per_step": e0.elapsed_time(e1) / steps, "recovery": rec(X)}
     return {"workload": "matrix completion 4096x4096, rank 20, Bernoulli(0.2) mask, "
                         "lambda = 0.02 ||P_Omega(M)||_2, proximal gradient with step 1",
             "steps": steps, "ms_per_step": ms / steps, "recovery": rec_host,
-            "device_loop": device_loop,
+            "device_loop": device_loop, "autotuned_schedule": tuned,
             "recovery_at_svd_steps": rec_at,
             "torch_svd_loop": {"steps": svd_steps, "ms_per_step": ms_svd / svd_steps,
                                "recovery": rec(Xs)},
