@@ -643,7 +643,7 @@ def run_ours(args, n):
         time.sleep(0.3)
     clocks = sampler.stop(t_start, t_end)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tc_ms, tc_flops, tc_n = ctx.profile_read()
+    tc_ms, tc_flops, tc_tensor_flops, tc_n = ctx.profile_read_ex()
     ctx.profile(False)
     launches = ctx.launch_count() - launches0
     st = int(status.item())
@@ -730,7 +730,13 @@ def run_ours(args, n):
         "roofline": {"bound": "tensor", "kernel": "tc_gemm_kernel", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": f"{src} bf16_tflops_sustained", "traffic": traffic,
-                     "launches": tc_n, "kernel_ms_total": tc_ms},
+                     "launches": tc_n, "kernel_ms_total": tc_ms,
+                     # what the tensor cores execute: hi/lo segments of the FP32-class
+                     # products, whole (diagonal, padded) tiles
+                     "executed_tflops": tc_tensor_flops / (tc_ms / 1e3) / 1e12 if tc_ms else 0.0,
+                     "executed_frac": (tc_tensor_flops / (tc_ms / 1e3) / 1e12 / peak
+                                       if tc_ms else 0.0),
+                     "executed_over_algorithmic": tc_tensor_flops / tc_flops if tc_flops else 0.0},
         "vs_fp32": {"library_fp32_tier_solves_per_s": fp32_tier,
                     "torch_plain_fp32_solves_per_s": plain,
                     "speedup_vs_library_fp32_tier": value / world / fp32_tier,

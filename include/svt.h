@@ -387,6 +387,12 @@ uint64_t svt_ctx_launch_count(svt_ctx_t ctx);
 svt_status svt_ctx_profile(svt_ctx_t ctx, int enable);
 svt_status svt_ctx_profile_read(svt_ctx_t ctx, double *tc_ms, double *tc_flops,
                                 uint64_t *tc_launches);
+/* As svt_ctx_profile_read, plus (nullable) the flops the tensor cores executed in
+ * those launches: every hi/lo segment product, whole tiles (the padding and the
+ * diagonal tiles of symmetric products) and K rounded up to 64. Their ratio to the
+ * algorithmic flops is the cost of the FP32-class products and of the tiling. */
+svt_status svt_ctx_profile_read_ex(svt_ctx_t ctx, double *tc_ms, double *tc_flops,
+                                   double *tc_tensor_flops, uint64_t *tc_launches);
 
 /*
  * Autotuner for the product kernel's tiles. Runs the svt_polar_ex solve of this A

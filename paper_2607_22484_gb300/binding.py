@@ -41,6 +41,7 @@ EXPORTS = [
     "svt_ctx_launch_count",
     "svt_ctx_profile", "svt_ctx_profile_read", "svt_polar_noalloc", "svt_autotune",
     "svt_prox_grad_step", "svt_complete", "svt_autotune_schedule", "svt_autotune_batch",
+    "svt_ctx_profile_read_ex",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -153,6 +154,10 @@ def lib():
         L.svt_ctx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_uint64)]
+        L.svt_ctx_profile_read_ex.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_uint64)]
         for name in EXPORTS:
             if name not in ("svt_status_str", "svt_options_default", "svt_ctx_launch_count"):
                 getattr(L, name).restype = ctypes.c_int
@@ -565,3 +570,12 @@ class Context:
         _check(lib().svt_ctx_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(fl),
                                           ctypes.byref(n)), "svt_ctx_profile_read")
         return ms.value, fl.value, int(n.value)
+
+    def profile_read_ex(self):
+        """(device ms, algorithmic flops, executed tensor flops, launches) of the
+        tensor-core launches since the last reset (svt_ctx_profile_read_ex)."""
+        ms, fl, tfl, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+        _check(lib().svt_ctx_profile_read_ex(self.handle, ctypes.byref(ms), ctypes.byref(fl),
+                                             ctypes.byref(tfl), ctypes.byref(n)),
+               "svt_ctx_profile_read_ex")
+        return ms.value, fl.value, tfl.value, int(n.value)

@@ -94,6 +94,10 @@ struct Plan {
     std::vector<F64Launch> f64;
     std::vector<PatchRec> patches;
     std::vector<double> tc_flops;   // algorithmic flops of each tensor-core launch
+    // flops the tensor cores execute for each launch: every hi/lo segment, whole tiles
+    // (padding, the diagonal tiles of symmetric products), K rounded up to 64
+    std::vector<double> tc_tensor_flops;
+    double fused_tensor_flops = 0.0;
     std::vector<int> tc_chain;      // per problem of each launch: 0 P chain, 1 S chain, 2 both
     // Per problem of each launch: the buffers it reads and writes (device addresses of
     // their hi parts; null = none or the caller's), for the fused solve's dependencies.
@@ -196,7 +200,7 @@ struct svt_ctx {
     // Optional per-launch timing of the tensor-core kernel (svt_ctx_profile).
     bool profile = false;
     std::vector<cudaEvent_t> prof_pool;
-    struct ProfRec { cudaEvent_t a, b; double flops; };
+    struct ProfRec { cudaEvent_t a, b; double flops, tensor_flops; };
     std::vector<ProfRec> prof_pending;
     size_t prof_next = 0;
     std::map<svt::TuneKey, std::vector<int>> tuning;  // svt_autotune results

@@ -406,10 +406,18 @@ struct Builder {
         l.tile_start[prods.size()] = start;
         // Algorithmic flops: 2 M N K per product, symmetric products counted at half;
         // the hi/lo segments of FP32-class products are not counted again.
-        double fl = 0.0;
+        double fl = 0.0, tfl = 0.0;
         for (const Prod &q : prods)
             fl += (q.sym ? 1.0 : 2.0) * (double)q.M * (double)q.N * (double)q.K;
+        for (int i = 0; i < l.nprob; ++i) {
+            const TcProblem &tp = l.p[i];
+            const double kpad = (double)((tp.K + kBK - 1) / kBK * kBK);
+            // each CTA tile: 128 rows x tile_cols(bn) columns over the padded K
+            tfl += (double)tp.nseg * (double)tc_valid_ctas(tp, bn) * 2.0 * kBM *
+                   (double)tile_cols(bn) * kpad;
+        }
         plan->tc_flops.push_back(fl);
+        plan->tc_tensor_flops.push_back(tfl);
         plan->ops.push_back({OP_TC, (int)plan->tc.size(), bn});
         plan->tc.push_back(l);
         plan->kernel_launches += 1;
@@ -750,7 +758,7 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
             err = tc_gemm_launch_fused(l, P.fused_bn, P.fused_tiles, grid_sms, s, P.uses_strips);
             if (prof) {
                 cudaEventRecord(e1, s);
-                ctx->prof_pending.push_back({e0, e1, P.fused_flops});
+                ctx->prof_pending.push_back({e0, e1, P.fused_flops, P.fused_tensor_flops});
             }
             ++launched;
             if (err != cudaSuccess)
@@ -820,7 +828,7 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
             err = tc_gemm_launch(l, op.bn, grid_sms, s);
             if (prof) {
                 cudaEventRecord(e1, s);
-                ctx->prof_pending.push_back({e0, e1, P.tc_flops[op.idx]});
+                ctx->prof_pending.push_back({e0, e1, P.tc_flops[op.idx], P.tc_tensor_flops[op.idx]});
             }
             break;
         }
@@ -1001,6 +1009,9 @@ svt_status build_fused(svt_ctx *ctx, Plan &P)
     P.fused_flops = 0.0;
     for (double f : P.tc_flops)
         P.fused_flops += f;
+    P.fused_tensor_flops = 0.0;
+    for (double f : P.tc_tensor_flops)
+        P.fused_tensor_flops += f;
     P.fused = true;
     return SVT_OK;
 }
@@ -1404,13 +1415,13 @@ svt_status svt_ctx_profile(svt_ctx_t ctx, int enable)
     return SVT_OK;
 }
 
-svt_status svt_ctx_profile_read(svt_ctx_t ctx, double *tc_ms, double *tc_flops,
-                                uint64_t *tc_launches)
+svt_status svt_ctx_profile_read_ex(svt_ctx_t ctx, double *tc_ms, double *tc_flops,
+                                   double *tc_tensor_flops, uint64_t *tc_launches)
 {
     if (!ctx || !tc_ms || !tc_flops || !tc_launches)
         return SVT_ERR_INVALID;
     std::lock_guard<std::mutex> g(ctx->mu);
-    double ms = 0.0, fl = 0.0;
+    double ms = 0.0, fl = 0.0, tfl = 0.0;
     for (auto &r : ctx->prof_pending) {
         if (cudaEventSynchronize(r.b) != cudaSuccess)
             return SVT_ERR_CUDA;
@@ -1419,13 +1430,22 @@ svt_status svt_ctx_profile_read(svt_ctx_t ctx, double *tc_ms, double *tc_flops,
             return SVT_ERR_CUDA;
         ms += t;
         fl += r.flops;
+        tfl += r.tensor_flops;
     }
     *tc_ms = ms;
     *tc_flops = fl;
+    if (tc_tensor_flops)
+        *tc_tensor_flops = tfl;
     *tc_launches = ctx->prof_pending.size();
     ctx->prof_pending.clear();
     ctx->prof_next = 0;
     return SVT_OK;
+}
+
+svt_status svt_ctx_profile_read(svt_ctx_t ctx, double *tc_ms, double *tc_flops,
+                                uint64_t *tc_launches)
+{
+    return svt_ctx_profile_read_ex(ctx, tc_ms, tc_flops, nullptr, tc_launches);
 }
 
 svt_status svt_debug_gemm_bf16_ex(svt_ctx_t ctx, int nseg, const void *L_hi, const void *L_lo,

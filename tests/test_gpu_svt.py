@@ -268,3 +268,24 @@ def test_strip_dependencies_match_oracle(shape):
     assert int(status.item()) == 0
     assert oracle.relerr(y1.cpu().numpy(), y0.cpu().numpy()) < 1e-5
     assert oracle.relerr(y1.cpu().numpy(), exact) < TOL["bf16"]
+
+
+def test_profile_counts_executed_tensor_work(ctx):
+    """svt_ctx_profile_read_ex: the executed tensor flops (hi/lo segments, whole tiles)
+    are at least the algorithmic flops, by the factor the FP32-class products and the
+    diagonal tiles add (between 1 and 2 for a BF16-tier solve)."""
+    a = _gap_matrix(1024, 1024, seed=25)
+    dev = torch.from_numpy(a).cuda()
+    ctx.polar(dev, 0.3, iters=20, prec="bf16")
+    ctx.profile(True)
+    ctx.polar(dev, 0.3, iters=20, prec="bf16")
+    ms, fl, tfl, n = ctx.profile_read_ex()
+    ctx.profile(False)
+    assert n >= 1 and ms > 0.0
+    assert fl > 0.0 and 1.0 < tfl / fl < 2.0, (fl, tfl)
+    # the algorithmic count is the one svt_ctx_profile_read reports
+    ctx.profile(True)
+    ctx.polar(dev, 0.3, iters=20, prec="bf16")
+    ms2, fl2, n2 = ctx.profile_read()
+    ctx.profile(False)
+    assert fl2 == fl and n2 == n
