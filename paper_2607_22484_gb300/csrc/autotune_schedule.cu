@@ -50,12 +50,6 @@ __global__ void __launch_bounds__(256) deviation_kernel(const float *Y, int64_t 
     }
 }
 
-bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes)
-{
-    const char *a0 = static_cast<const char *>(a), *b0 = static_cast<const char *>(b);
-    return a0 < b0 + bbytes && b0 < a0 + abytes;
-}
-
 } // namespace
 
 extern "C" svt_status svt_autotune_schedule(svt_ctx_t ctx, const float *A, int64_t m, int64_t n,

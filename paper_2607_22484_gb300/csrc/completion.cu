@@ -183,12 +183,6 @@ __global__ void step_decide_kernel(svt_completion_stats *st, cudaGraphConditiona
     cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
-bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes)
-{
-    const char *a0 = static_cast<const char *>(a), *b0 = static_cast<const char *>(b);
-    return a0 < b0 + bbytes && b0 < a0 + abytes;
-}
-
 } // namespace
 
 extern "C" svt_status svt_prox_grad_step(svt_ctx_t ctx, float *X, int64_t ldx, const float *M,
@@ -205,9 +199,9 @@ extern "C" svt_status svt_prox_grad_step(svt_ctx_t ctx, float *X, int64_t ldx, c
         return SVT_ERR_INVALID;
     // Z is written before X is read back by the solve: it may alias none of the inputs.
     const size_t zb = (size_t)((m - 1) * ldz + n) * sizeof(float);
-    if (overlaps(Z, zb, X, (size_t)((m - 1) * ldx + n) * sizeof(float)) ||
-        overlaps(Z, zb, M, (size_t)((m - 1) * ldm + n) * sizeof(float)) ||
-        overlaps(Z, zb, mask, (size_t)((m - 1) * ldw + n)))
+    if (svt::overlaps(Z, zb, X, (size_t)((m - 1) * ldx + n) * sizeof(float)) ||
+        svt::overlaps(Z, zb, M, (size_t)((m - 1) * ldm + n) * sizeof(float)) ||
+        svt::overlaps(Z, zb, mask, (size_t)((m - 1) * ldw + n)))
         return SVT_ERR_INVALID;
     // Everything the solve checks (sizes, options, workspace) before any launch.
     svt::Resolved r;

@@ -181,6 +181,13 @@ struct CallArgs {
 svt_status validate(const float *A, int64_t m, int64_t n, int64_t lda, float tau, const float *Y,
                     int64_t ldy);
 
+// Whether the byte ranges [a, a + abytes) and [b, b + bbytes) intersect.
+inline bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes)
+{
+    const char *a0 = static_cast<const char *>(a), *b0 = static_cast<const char *>(b);
+    return a0 < b0 + bbytes && b0 < a0 + abytes;
+}
+
 struct CompletionGraph;  // completion.cu
 
 } // namespace svt
