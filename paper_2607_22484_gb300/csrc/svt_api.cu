@@ -131,7 +131,7 @@ bool resolve(const svt_options *in, Resolved *r)
         o = *in;
     else
         svt_options_default(&o);
-    if (o.iters < 0 || o.iters > 1000)
+    if (o.iters < 0 || o.iters > 1000 || !std::isfinite(o.ell0) || !std::isfinite(o.delta))
         return false;
     if (o.prec != SVT_FP64 && o.prec != SVT_FP32 && o.prec != SVT_BF16)
         return false;

@@ -120,3 +120,23 @@ def test_complete_rejects_null_arguments_on_the_host():
     st = lib.svt_complete(None, None, 4, None, 4, None, 4, None, 4, None, 4, 4, 4,
                           ctypes.byref(prm), None, None, None)
     assert pkg.status_str(st) == "SVT_ERR_INVALID"
+
+
+@pytest.mark.parametrize("bad", [
+    {"iters": -1}, {"iters": 1001}, {"prec": 9}, {"schedule": 7}, {"norm": 5},
+    {"ell0": 1.0}, {"ell0": float("nan")}, {"delta": float("inf")}, {"mode": 2},
+    {"hp_steps": -2}, {"tile": 300}, {"tile": 64},
+])
+def test_option_validation_on_the_host(bad):
+    """Options outside their ranges are rejected before any device work (the sizing
+    call runs the same resolution as every entry point)."""
+    with pytest.raises(pkg.SVTError) as e:
+        pkg.workspace_bytes(256, 256, **bad)
+    assert e.value.status == pkg.binding.ERR_INVALID
+
+
+def test_valid_option_corners_on_the_host():
+    for ok in ({"iters": 0}, {"iters": 1000}, {"tile": 128}, {"tile": 256}, {"tile": 512},
+               {"ell0": 0.0}, {"delta": 0.0}, {"hp_steps": -1}, {"schedule": "ns3"},
+               {"prec": "fp64", "tile": 512}):
+        assert pkg.workspace_bytes(256, 256, **ok) > 0
