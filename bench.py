@@ -765,6 +765,31 @@ def run_ours(args, n):
     return 0
 
 
+def run_batch_only(count):
+    """The batch recipe's first `count` matrices (sizes log-uniform 128-1024), BF16 tier,
+    20 steps, one svt_batch call three times; prints the last call's time."""
+    import torch
+    import paper_2607_22484_gb300 as pkg
+    import svt_workloads as wl
+    dev = torch.device("cuda:0")
+    items = wl.batch_recipe(count)
+    As = [torch.from_numpy(it.matrix()).to(dev) for it in items]
+    taus = [it.tau for it in items]
+    outs = [torch.empty_like(a) for a in As]
+    ctx = pkg.Context(0, workspace_bytes=1 << 20)
+    opts = {"iters": ITERS, "prec": "bf16"}
+    for _ in range(2):
+        ctx.batch(As, taus, outs=outs, opts=opts)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record()
+    ctx.batch(As, taus, outs=outs, opts=opts)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"batch_only": count, "ms": e0.elapsed_time(e1)}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -789,9 +814,14 @@ def main():
                     help="skip the batch and serving measurements")
     ap.add_argument("--only-timed", action="store_true",
                     help="run only the warm-up and timed solves (for profiler launch lists)")
+    ap.add_argument("--batch-only", type=int, default=0, metavar="COUNT",
+                    help="run only a grouped batch of COUNT matrices of the batch recipe, "
+                         "three times (for profiling the batch launch)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.size)
+    if args.batch_only:
+        return run_batch_only(args.batch_only)
     return run_ours(args, args.size)
 
 
