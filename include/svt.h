@@ -370,6 +370,15 @@ svt_status svt_debug_gemm_bf16_ex(svt_ctx_t ctx, int nseg, const void *L_hi, con
                                   int64_t K, int64_t ldl, int64_t ldr, float *D, int64_t ldd,
                                   int sym, int tile, void *stream);
 
+/* Failure-path check of the device-side bounded waits: launches the product kernel
+ * (fused form) on a one-tile table whose tile waits for its own completion, so the
+ * wait runs out (about 2 s); the kernel records SVT_ERR_TIMEOUT in *d_status (device
+ * word, initially SVT_OK), releases its resources and returns, and the context stays
+ * usable. Overwrites the start of the context's workspace (any later solve restores
+ * what it needs). Errors: SVT_ERR_INVALID, SVT_ERR_OOM (a workspace smaller than
+ * the one-tile table), SVT_ERR_BUSY, SVT_ERR_CUDA. */
+svt_status svt_debug_wait_timeout(svt_ctx_t ctx, svt_status *d_status, void *stream);
+
 /* Number of kernel launches the library has issued on this context so far
  * (host counter; used to report launches per solve). */
 uint64_t svt_ctx_launch_count(svt_ctx_t ctx);

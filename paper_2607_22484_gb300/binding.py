@@ -41,7 +41,7 @@ EXPORTS = [
     "svt_ctx_launch_count",
     "svt_ctx_profile", "svt_ctx_profile_read", "svt_polar_noalloc", "svt_autotune",
     "svt_prox_grad_step", "svt_complete", "svt_autotune_schedule", "svt_autotune_batch",
-    "svt_ctx_profile_read_ex",
+    "svt_ctx_profile_read_ex", "svt_debug_wait_timeout",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -144,6 +144,7 @@ def lib():
         L.svt_autotune_batch.argtypes = [vp, ctypes.POINTER(Matrix), i32, i32, vp,
                                          ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_double)]
+        L.svt_debug_wait_timeout.argtypes = [vp, vp, vp]
         L.svt_ctx_launch_count.argtypes = [vp]
         L.svt_ctx_launch_count.restype = ctypes.c_uint64
         L.svt_ctx_profile.argtypes = [vp, i32]
@@ -560,6 +561,13 @@ class Context:
 
     def launch_count(self) -> int:
         return int(lib().svt_ctx_launch_count(self.handle))
+
+    def debug_wait_timeout(self, status, stream=None):
+        """svt_debug_wait_timeout: a product-kernel launch whose bounded wait runs out;
+        `status` (CUDA int32 tensor, zero) receives SVT_ERR_TIMEOUT."""
+        _check(lib().svt_debug_wait_timeout(self.handle, ctypes.c_void_p(status.data_ptr()),
+                                            ctypes.c_void_p(_stream_ptr(stream))),
+               "svt_debug_wait_timeout")
 
     def profile(self, enable: bool = True):
         _check(lib().svt_ctx_profile(self.handle, 1 if enable else 0), "svt_ctx_profile")

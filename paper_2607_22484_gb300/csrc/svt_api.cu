@@ -1502,6 +1502,51 @@ svt_status svt_debug_gemm_bf16_ex(svt_ctx_t ctx, int nseg, const void *L_hi, con
     return e == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;
 }
 
+svt_status svt_debug_wait_timeout(svt_ctx_t ctx, svt_status *d_status, void *stream)
+{
+    if (!ctx || !d_status)
+        return SVT_ERR_INVALID;
+    // [one problem | tile starts 0, 1 | done[0], tile counter] at the workspace start
+    const size_t tab = align_up(sizeof(TcProblem), kAlign);
+    const size_t bytes = tab + 4 * sizeof(int);
+    if (ctx->ws_bytes < bytes)
+        return SVT_ERR_OOM;
+    if (serve_busy(ctx))
+        return SVT_ERR_BUSY;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    std::vector<uint8_t> img(bytes, 0);
+    TcProblem &p = *reinterpret_cast<TcProblem *>(img.data());
+    p.M = p.N = p.K = kBM;
+    p.tiles_m = p.tiles_n = 1;
+    p.nseg = 1;
+    p.pid = 0;
+    p.dep[0] = 0;  // the tile waits for its own problem to complete: it never does
+    p.dep_target[0] = 1;
+    p.dep[1] = -1;
+    p.strip_base = -1;
+    p.ep.alpha = 1.0;
+    p.ep.status = reinterpret_cast<int *>(d_status);
+    int *ints = reinterpret_cast<int *>(img.data() + tab);
+    ints[0] = 0;
+    ints[1] = 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ctx->table_owner = nullptr;  // the workspace start is overwritten
+    if (cudaMemcpyAsync(ctx->ws, img.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    TcLaunch l;
+    std::memset(&l, 0, sizeof(l));
+    l.gtab = reinterpret_cast<const TcProblem *>(ctx->ws);
+    l.gstart = reinterpret_cast<const int *>(ctx->ws + tab);
+    l.gcount = 1;
+    l.done = reinterpret_cast<int *>(ctx->ws + tab) + 2;
+    l.tile_counter = l.done + 1;
+    const cudaError_t e = tc_gemm_launch_fused(l, 128, 1, ctx->num_sms, s, false);
+    ctx->launches += 1;
+    return e == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;
+}
+
 svt_status svt_debug_gemm_bf16(svt_ctx_t ctx, int nseg, const void *L_hi, const void *L_lo,
                                const void *R_hi, const void *R_lo, int64_t M, int64_t N,
                                int64_t K, int64_t ldl, int64_t ldr, float *D, int64_t ldd,

@@ -150,3 +150,83 @@ def test_largest_row_count(ctx, wide):
     rel = (err2 / ref2) ** 0.5
     print(f"{'1024 x 2^20' if wide else '2^20 x 1024'} BF16 relerr {rel:.3e}")
     assert rel < 2e-2
+
+
+# --- guard bands (the stand-in for a memory checker) and the device-side timeout path
+
+SENTINEL = 0x7FC0BEEF  # a NaN bit pattern that no kernel writes
+
+
+def _gap(m, n, seed, tau=0.3):
+    rng = np.random.default_rng(seed)
+    k = min(m, n)
+    lo = np.sort(rng.uniform(0.01, tau - 0.06, k // 2))
+    hi = np.sort(rng.uniform(tau + 0.06, 1.0, k - k // 2 - 1))
+    sig = np.sort(np.concatenate([lo, hi, [1.0]]))[::-1]
+    import svt_workloads as wl
+    return wl.spectrum_matrix(sig, m, n, seed)
+
+
+def _guarded(m, n):
+    """An m x n float view inside a larger buffer filled with SENTINEL, and the mask of
+    the guard cells."""
+    big = torch.full((m + 4, n + 12), SENTINEL, dtype=torch.int32, device="cuda")
+    guard = torch.ones(big.shape, dtype=torch.bool, device="cuda")
+    guard[2:2 + m, 5:5 + n] = False
+    return big, big.view(torch.float32)[2:2 + m, 5:5 + n], guard
+
+
+@pytest.mark.parametrize("m,n,prec", [(300, 200, "bf16"), (200, 300, "fp32"), (520, 130, "bf16")])
+def test_guard_bands_around_output_and_workspace(m, n, prec):
+    """Outputs written into views of larger sentinel-filled buffers, a sentinel tail after
+    the workspace the solve sizes, the input compared before and after: every guard
+    cell and the input are untouched, and the result is right."""
+    a = _gap(m, n, m + n)
+    exact = oracle.svt_definition(a.astype(np.float64), 0.3)
+    need = pkg.workspace_bytes(m, n, iters=20, prec=prec)
+    ctx = pkg.Context(0, workspace_bytes=need + (1 << 20))
+    ctx.workspace[need:].fill_(0xA5)
+    A = torch.from_numpy(a).cuda()
+    A0 = A.clone()
+    big, Y, guard = _guarded(m, n)
+    ctx.polar(A, 0.3, out=Y, iters=20, prec=prec)
+    torch.cuda.synchronize()
+    assert torch.equal(A, A0)
+    assert bool((big[guard] == SENTINEL).all())
+    assert bool((ctx.workspace[need:] == 0xA5).all())
+    tol = 2e-2 if prec == "bf16" else 1e-4
+    assert oracle.relerr(Y.cpu().numpy().astype(np.float64), exact) < tol
+
+
+def test_guard_bands_around_batch_outputs():
+    shapes = [(96, 64), (130, 260), (200, 200), (64, 128)]
+    mats = [_gap(m, n, 7 + i) for i, (m, n) in enumerate(shapes)]
+    ctx = pkg.Context(0, workspace_bytes=1 << 20)
+    As = [torch.from_numpy(a).cuda() for a in mats]
+    guarded = [_guarded(m, n) for m, n in shapes]
+    ctx.batch(As, [0.3] * len(As), outs=[g[1] for g in guarded], opts={"iters": 20, "prec": "bf16"})
+    torch.cuda.synchronize()
+    for a, (big, Y, guard) in zip(mats, guarded):
+        assert bool((big[guard] == SENTINEL).all())
+        exact = oracle.svt_definition(a.astype(np.float64), 0.3)
+        assert oracle.relerr(Y.cpu().numpy().astype(np.float64), exact) < 2e-2
+
+
+def test_device_wait_timeout_is_reported_and_the_context_recovers():
+    """A tile that waits for its own completion: the bounded wait runs out (~2 s), the
+    kernel records SVT_ERR_TIMEOUT and returns without trapping, and later solves on
+    the same context are correct."""
+    import time
+    ctx = pkg.Context(0, workspace_bytes=16 << 20)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    t0 = time.time()
+    ctx.debug_wait_timeout(st)
+    torch.cuda.synchronize()
+    dt = time.time() - t0
+    assert int(st.item()) == pkg.binding.ERR_TIMEOUT
+    assert 1.5 < dt < 30, dt
+    a = _gap(96, 64, 3)
+    y = ctx.polar(torch.from_numpy(a).cuda(), 0.3, iters=20, prec="bf16")
+    torch.cuda.synchronize()
+    assert oracle.relerr(y.cpu().numpy().astype(np.float64),
+                         oracle.svt_definition(a.astype(np.float64), 0.3)) < 2e-2
