@@ -180,3 +180,16 @@ def test_continuation_degenerate_cases():
         oc.complete_continuation(m, mask, lam, 0.5 * lam, 0.5, 0.0, 3)
     with pytest.raises(ValueError):
         oc.complete_continuation(m, mask, lam, lam0, 1.0, 0.0, 3)
+
+
+def test_continuation_stops_exactly_when_the_iterate_stays_zero():
+    """A stage whose lambda exceeds sigma_max of P_Omega(M) (the first step from X = 0
+    thresholds everything) ends after one step with change 0: the zero iterate is that
+    stage's fixed point, whatever tol is."""
+    m, mask, lam, _ = _cont_instance(17)
+    s0 = np.linalg.norm(m * mask, 2)
+    x, info = oc.complete_continuation(m, mask, lam, 2.0 * s0, 0.5, 0.0, 50, stage_steps=10)
+    st = np.array(info["stage_of_step"])
+    assert np.sum(st == 0) == 1 and info["changes"][0] == 0.0 and info["rhos"][0] == 0.0
+    # the next stages move
+    assert info["changes"][-1] > 0.0 or info["steps"] > 1
