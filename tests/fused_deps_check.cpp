@@ -253,8 +253,10 @@ bool simulate(const std::vector<Buffer> &bufs, const std::vector<Product> &ps, b
 
 // The products of one solve, in the plan builder's order (tall problem M x N in
 // blocks): Gram, per step Y, Z, X Z for the P chain and S^2, Y^2, S Z for the S chain,
-// the polish of both chains and the combine.
-void solve_sequence(int Tm, int T, int steps, std::vector<Buffer> &bufs, std::vector<Product> &ps)
+// the polish of both chains and the combine. skip_p: Corollary 1's mode, no P chain (B
+// is A, written before the launch).
+void solve_sequence(int Tm, int T, int steps, std::vector<Buffer> &bufs, std::vector<Product> &ps,
+                    bool skip_p = false)
 {
     enum { X0, X1, Xt0, Xt1, S0, S1, Yp, Zp, Ys, Zs, ZPp, ZSp, B, Sp, NB };
     bufs.assign(NB, {T, T});
@@ -274,22 +276,29 @@ void solve_sequence(int Tm, int T, int steps, std::vector<Buffer> &bufs, std::ve
     const int X[2] = {X0, X1}, Xt[2] = {Xt0, Xt1}, S[2] = {S0, S1};
     for (int s = 0; s < steps; ++s) {
         const int nxt = 1 - cur;
-        sq(Xt[cur], Xt[cur], -1, Yp, 0, -1, s == 0 ? NRM_YP : -1);
+        if (!skip_p)
+            sq(Xt[cur], Xt[cur], -1, Yp, 0, -1, s == 0 ? NRM_YP : -1);
         sq(S[cur], S[cur], -1, Ys, 1, -1, s == 0 ? NRM_YS : -1);
-        sq(Yp, Yp, Yp, Zp, 0, s == 0 ? NRM_YP : -1, -1);
+        if (!skip_p)
+            sq(Yp, Yp, Yp, Zp, 0, s == 0 ? NRM_YP : -1, -1);
         sq(Ys, Ys, Ys, Zs, 1, s == 0 ? NRM_YS : -1, -1);
-        Product xz;
-        xz.l = X[cur], xz.r = Zp, xz.o = X[nxt], xz.t = Xt[nxt], xz.chain = 0;
-        xz.tiles_m = Tm, xz.tiles_n = T;
-        ps.push_back(xz);
+        if (!skip_p) {
+            Product xz;
+            xz.l = X[cur], xz.r = Zp, xz.o = X[nxt], xz.t = Xt[nxt], xz.chain = 0;
+            xz.tiles_m = Tm, xz.tiles_n = T;
+            ps.push_back(xz);
+        }
         sq(S[cur], Zs, -1, S[nxt], 1, -1, -1);
         cur = nxt;
     }
-    sq(Xt[cur], Xt[cur], -1, ZPp, 0, -1, -1);
+    if (!skip_p)
+        sq(Xt[cur], Xt[cur], -1, ZPp, 0, -1, -1);
     sq(S[cur], S[cur], -1, ZSp, 1, -1, -1);
-    Product pb;
-    pb.l = X[cur], pb.r = ZPp, pb.o = B, pb.chain = 0, pb.tiles_m = Tm, pb.tiles_n = T;
-    ps.push_back(pb);
+    if (!skip_p) {
+        Product pb;
+        pb.l = X[cur], pb.r = ZPp, pb.o = B, pb.chain = 0, pb.tiles_m = Tm, pb.tiles_n = T;
+        ps.push_back(pb);
+    }
     sq(S[cur], ZSp, -1, Sp, 1, -1, -1);
     Product comb;  // output to the caller's Y: no buffer of the launch
     comb.l = B, comb.r = Sp, comb.c = B, comb.chain = 2, comb.tiles_m = Tm, comb.tiles_n = T;
@@ -340,9 +349,9 @@ int main(int argc, char **argv)
     std::vector<Product> ps;
     int sims = 0;
     // the solve's own sequence, both modes, square and tall, plain and paired tiles
-    for (int shape = 0; shape < 4; ++shape) {
-        const int T = 2 + shape % 2, Tm = shape < 2 ? T : 2 * T;
-        solve_sequence(Tm, T, 3, bufs, ps);
+    for (int shape = 0; shape < 8; ++shape) {
+        const int T = 2 + shape % 2, Tm = (shape & 2) ? 2 * T : T;
+        solve_sequence(Tm, T, 3, bufs, ps, shape >= 4);  // shapes 4-7: no P chain
         for (bool strips : {false, true})
             for (int ctas : {1, 2})
                 for (int r = 0; r < rounds; ++r) {

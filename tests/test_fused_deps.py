@@ -5,8 +5,8 @@ fused launches at block granularity under random interleavings of all tiles whos
 conditions hold: every read must see the version program order implies, no write may
 clobber a block an earlier reader still needs, norms must be complete before scales
 read them, and no launch may stall. It runs the solve's own product sequence (chain
-and strip modes, square and tall, one and two CTAs per tile) and random product
-sequences in strip mode. Planting a mistake in the header (dropping the WAR
+and strip modes, square and tall, one and two CTAs per tile, with and without the P
+chain of Corollary 1's mode) and random product sequences in strip mode. Planting a mistake in the header (dropping the WAR
 conditions, letting the combine ignore one chain, a strip target one tile short)
 makes it fail by the thousands.
 """
