@@ -476,7 +476,14 @@ svt_status svt_autotune_batch(svt_ctx_t ctx, const svt_matrix *mats, int count, 
  *   A, m, n, lda, tau, opt, Y, ldy, d_status, stream: as svt_polar_ex.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and sets up an internal context; make that first call
- * before any stream capture. All calls share the one array and it keeps the
+ * before any stream capture. The first call for each new shape and option set
+ * also builds a launch plan, which allocates a small pinned host buffer
+ * (cudaMallocHost, a few KB per product of the solve) that later calls copy the
+ * launch table from; that allocation may synchronise the device and is not
+ * allowed under capture, so make those calls before any capture as well. The
+ * internal context caches up to 64 plans; a call that finds 64 cached waits for
+ * the device (cudaDeviceSynchronize) and drops them. All calls share the one
+ * array and it keeps the
  * last call's contents (the solve re-initialises what must start at zero), so
  * calls whose GPU work overlaps -- on different streams or from different
  * threads without ordering -- race and corrupt each other's results.

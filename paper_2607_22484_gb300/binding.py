@@ -216,18 +216,22 @@ def polar_noalloc(A, tau: float, out=None, status=None, stream=None, **opts):
     the library (scratch is a fixed 32 MiB device array shared by all calls).
     ``out`` should be preallocated by callers that cannot allocate."""
     import torch
-    a_ptr, m, n, lda = _f32_matrix(A, "A")
+    a_ptr, m, n, lda = _f32_matrix(A, "A")  # rejects host tensors
     if out is None:
         out = torch.empty((m, n), dtype=torch.float32, device=A.device)
     y_ptr, ym, yn, ldy = _f32_matrix(out, "out")
     if (ym, yn) != (m, n):
         raise ValueError("out has the wrong shape")
+    if out.device != A.device:
+        raise ValueError("out must be on A's device")
     o = make_options(**opts)
     st_ptr = status.data_ptr() if status is not None else None
-    _check(lib().svt_polar_noalloc(A.device.index or 0, ctypes.c_void_p(a_ptr), m, n, lda,
+    # The library runs on A's device: the default stream is that device's current one.
+    s = torch.cuda.current_stream(A.device) if stream is None else stream
+    _check(lib().svt_polar_noalloc(A.device.index, ctypes.c_void_p(a_ptr), m, n, lda,
                                    ctypes.c_float(tau), ctypes.byref(o), ctypes.c_void_p(y_ptr),
                                    ldy, ctypes.c_void_p(st_ptr),
-                                   ctypes.c_void_p(_stream_ptr(stream))), "svt_polar_noalloc")
+                                   ctypes.c_void_p(int(s.cuda_stream))), "svt_polar_noalloc")
     return out
 
 
@@ -352,8 +356,9 @@ class Context:
                            stream=None, **opts):
         """Proximal-gradient completion as one device-resident loop (svt_complete):
         lambda continuation from lam0 (None: lam, one stage) by factor eta down to lam,
-        stages ending when ||X_new - X_old||_F / ||X_new||_F <= tol or after stage_steps
-        steps, at most max_steps steps in all. X is the starting point (zeros if None)
+        stages ending when ||X_new - X_old||_F / ||P_Omega(M)||_F <= tol (the change
+        measured against the data's scale, which stays meaningful when the iterate is
+        zero) or after stage_steps steps, at most max_steps steps in all. X is the starting point (zeros if None)
         and receives the result. Returns (X, stats): stats is a CUDA byte tensor holding
         svt_completion_stats (read_completion_stats parses it)."""
         import torch

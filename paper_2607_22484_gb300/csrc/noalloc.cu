@@ -19,6 +19,15 @@
 // status word, Gram diagonal) and overwrites every other buffer before reading
 // it. Calls whose work overlaps on the GPU (different streams, or another thread)
 // race on the array.
+//
+// Host memory: the first call for each shape and option set builds a launch
+// plan, whose one-launch problem table is kept as a small pinned host image
+// (cudaMallocHost, a few KB per product of the solve) that every later call
+// copies to the array. That allocation can synchronise the device and is not
+// allowed under stream capture, so such first calls belong before any capture.
+// The internal context keeps at most kMaxPlans plans: a call that finds that many
+// cached first waits for the device (their images may still be in copies) and
+// drops them all; they are rebuilt, with new pinned images, if used again.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -29,6 +38,7 @@ namespace {
 
 constexpr size_t kScratchBytes = SVT_NOALLOC_SCRATCH_BYTES;
 constexpr int kMaxDevices = 64;
+constexpr size_t kMaxPlans = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -81,6 +91,17 @@ extern "C" svt_status svt_polar_noalloc(int device, const float *A, int64_t m, i
             return st;
         }
         d.ready = true;
+    }
+    {
+        // Bound the pinned host images the cached plans hold (see the file comment).
+        std::lock_guard<std::mutex> pg(d.ctx->mu);
+        if (d.ctx->plans.size() >= kMaxPlans) {
+            if (cudaDeviceSynchronize() != cudaSuccess) {
+                cudaSetDevice(prev);
+                return SVT_ERR_CUDA;
+            }
+            svt::evict_plans(d.ctx, 0);
+        }
     }
     st = svt_polar_ex(d.ctx, A, m, n, lda, tau, opt, Y, ldy, d_status, stream);
     cudaSetDevice(prev);

@@ -206,3 +206,49 @@ def test_rank_deficient_any_partial_isometry():
     sgn = osvt.sign_of_shifted_gram(v, s, tau * tau)
     for p in (p1, p2):
         np.testing.assert_allclose(osvt.prop1_factored(a, p, sgn, tau), exact, atol=1e-12)
+
+
+# ------------------------------------------------ gap and the error metric's readings
+
+def test_gap_closed_form_on_diagonal_spectra():
+    """gap(tau) = min_i |sigma_i - tau| / sigma_max, with sigma read off the Jacobi SVD of
+    a diagonal matrix (so the values are exact). The nearest value sits above tau in the
+    first case and below it in the second; sigma_max differs from sigma_min in both, so
+    dividing by the wrong extreme, or taking the max distance, changes the value."""
+    for diag, tau, want in (([0.1, 1.0, 0.32, 0.5], 0.3, 0.02 / 1.0),
+                            ([2.0, 0.28, 0.9, 0.05], 0.3, 0.02 / 2.0),
+                            ([4.0, 1.0], 0.0, 1.0 / 4.0),
+                            ([3.0, 1.0], 5.0, 2.0 / 3.0)):
+        a = np.diag(np.array(diag, np.float64))
+        _, s, _ = oracle.jacobi_svd(a)
+        assert oracle.gap(s, tau) == pytest.approx(want, rel=1e-12), (diag, tau)
+    # tau on a singular value: zero gap
+    assert oracle.gap(np.array([1.0, 0.5]), 0.5) == 0.0
+    # the zero spectrum has no scale: nothing binds there
+    assert oracle.gap(np.zeros(3), 0.2) == float("inf")
+
+
+def test_gap_gates_the_tier_tolerance_on_the_64x64_recipe():
+    """The 64 x 64 recipe puts no singular value in [0.25, 0.35] around tau = 0.3 with
+    sigma_max = 1, so its gap is at least 0.05 (Section 3's workloads; the 5 % rule)."""
+    import svt_workloads as wl
+    _, s, _ = oracle.jacobi_svd(wl.spectrum_64().astype(np.float64))
+    g = oracle.gap(s, 0.3)
+    assert 0.05 <= g <= 0.07, g
+
+
+def test_relerr_zero_result_is_relative_to_A():
+    """Reading of the error metric when A_tau = 0 (tau >= sigma_max): the error is taken
+    relative to ||A||_F. A = diag(3, 4) has ||A||_F = 5; an approximation diag(0.3, 0.4)
+    of the zero result is 0.5 / 5 = 0.1 off."""
+    a = np.diag([3.0, 4.0])
+    exact = _svt(a, 4.5)
+    assert np.all(exact == 0.0)
+    approx = np.diag([0.3, 0.4])
+    assert oracle.relerr(approx, exact, a) == pytest.approx(0.1, rel=1e-15)
+    with pytest.raises(ValueError):
+        oracle.relerr(approx, exact)
+    # both A and the result zero: the absolute norm of the approximation
+    assert oracle.relerr(approx, np.zeros((2, 2)), np.zeros((2, 2))) == pytest.approx(0.5)
+    # a nonzero result uses its own norm, whatever A is: ||(1, 0) - (1, 1)|| / ||(1, 1)||
+    assert oracle.relerr(np.diag([1.0, 0.0]), np.eye(2), a) == pytest.approx(1 / np.sqrt(2))

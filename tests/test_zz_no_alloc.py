@@ -4,9 +4,12 @@ stopping at the first failure has already run every other test.
 
 Its output must match the ordinary entry point (svt_polar_ex with a caller
 workspace) within the tolerance the batch/serving tests use for "same solve"
-(1e-5 relative), on two calls in a row with different shapes (the shared array
-keeps the previous call's contents), and both must stay within the BF16 tier's
-2e-2 of the FP64 oracle."""
+(1e-5 relative), on calls in a row with different shapes and then the first shape
+again (the shared array keeps the previous call's contents, so the cached plan of
+the first shape runs over what the second left there), and all must stay within
+the BF16 tier's 2e-2 of the FP64 oracle. Once a shape has been solved, a further
+call allocates nothing on the device: the driver's free-memory count and torch's
+allocator counters are the same before and after it."""
 import numpy as np
 import pytest
 import torch
@@ -30,7 +33,7 @@ def _gap_matrix(m, n, seed, tau=0.3):
 
 def test_noalloc_matches_svt_polar_two_calls():
     ctx = pkg.Context(0, workspace_bytes=64 << 20)
-    for shape, seed in (((256, 192), 1), ((100, 300), 2)):
+    for shape, seed in (((256, 192), 1), ((100, 300), 2), ((256, 192), 1)):
         a = _gap_matrix(*shape, seed=seed)
         dev = torch.from_numpy(a).cuda()
         out = torch.full_like(dev, float("nan"))
@@ -50,3 +53,21 @@ def test_noalloc_rejects_sizes_beyond_scratch():
     with pytest.raises(pkg.SVTError) as e:
         pkg.polar_noalloc(a, 0.5, out=torch.empty_like(a))
     assert e.value.status == pkg.binding.ERR_UNSUPPORTED
+
+
+def test_noalloc_second_call_allocates_nothing():
+    a = torch.from_numpy(_gap_matrix(300, 260, seed=4)).cuda()
+    out = torch.empty_like(a)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    pkg.polar_noalloc(a, 0.3, out=out, status=status, iters=20, prec="bf16")  # plan, modules
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+    for _ in range(3):
+        pkg.polar_noalloc(a, 0.3, out=out, status=status, iters=20, prec="bf16")
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert int(status.item()) == 0
+    assert free1 == free0, (free0, free1)
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.memory_reserved() == reserved0
