@@ -195,6 +195,19 @@ svt_status svt_polar_ex(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int
                         svt_status *d_status, void *stream);
 
 /*
+ * svt_polar_f64: the FP64 tier's A_tau (Eq. 1 through Proposition 1, every step in
+ * FP64) stored in FP64, so that its accuracy is not capped by an FP32 output's
+ * rounding (~6e-8 relative).
+ *   A: m x n FP32 device (lda >= n), read only. Y: m x n FP64 device, row-major,
+ *   leading dimension ldy >= n, not overlapping A. opt: as svt_polar_ex; opt must
+ *   not be NULL and opt->prec must be SVT_FP64. Other arguments as svt_polar.
+ * Errors: as svt_polar_ex; SVT_ERR_INVALID when opt is NULL or names another tier.
+ */
+svt_status svt_polar_f64(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int64_t lda,
+                         float tau, const svt_options *opt, double *Y, int64_t ldy,
+                         svt_status *d_status, void *stream);
+
+/*
  * svt_batch: A_tau for `count` independent matrices of any sizes, enqueued on
  * `stream`. When all matrices share one option set with the default pipeline
  * (BF16 or FP32 tier, polish on, SVT mode), every product of every matrix (both

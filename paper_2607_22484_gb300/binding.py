@@ -41,7 +41,7 @@ EXPORTS = [
     "svt_ctx_launch_count",
     "svt_ctx_profile", "svt_ctx_profile_read", "svt_polar_noalloc", "svt_autotune",
     "svt_prox_grad_step", "svt_complete", "svt_autotune_schedule", "svt_autotune_batch",
-    "svt_ctx_profile_read_ex", "svt_debug_wait_timeout",
+    "svt_ctx_profile_read_ex", "svt_debug_wait_timeout", "svt_polar_f64",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -117,6 +117,8 @@ def lib():
         L.svt_polar.argtypes = [vp, vp, i64, i64, i64, ctypes.c_float, i32, i32, vp, i64, vp, vp]
         L.svt_polar_ex.argtypes = [vp, vp, i64, i64, i64, ctypes.c_float, ctypes.POINTER(Options),
                                    vp, i64, vp, vp]
+        L.svt_polar_f64.argtypes = [vp, vp, i64, i64, i64, ctypes.c_float,
+                                    ctypes.POINTER(Options), vp, i64, vp, vp]
         L.svt_batch.argtypes = [vp, ctypes.POINTER(Matrix), i32, vp]
         L.svt_batch_workspace_bytes.argtypes = [ctypes.POINTER(Matrix), i32,
                                                 ctypes.POINTER(ctypes.c_size_t)]
@@ -305,6 +307,27 @@ class Context:
                                   ctypes.c_float(tau), ctypes.byref(o), ctypes.c_void_p(y_ptr),
                                   ldy, ctypes.c_void_p(st_ptr), ctypes.c_void_p(_stream_ptr(stream))),
                "svt_polar_ex")
+        return out
+
+    def polar_f64(self, A, tau: float, out=None, status=None, stream=None, **opts):
+        """Y = A_tau in FP64 from the FP64 tier through svt_polar_f64 (asynchronous on
+        the current stream). A: CUDA float32; out: CUDA float64 (allocated if None)."""
+        import torch
+        a_ptr, m, n, lda = _f32_matrix(A, "A")
+        if out is None:
+            out = torch.empty((m, n), dtype=torch.float64, device=A.device)
+        if (not isinstance(out, torch.Tensor) or out.dtype != torch.float64 or not out.is_cuda
+                or out.dim() != 2 or tuple(out.shape) != (m, n) or out.stride(1) != 1):
+            raise ValueError("out must be a row-major CUDA float64 tensor of A's shape")
+        opts = dict(opts, prec="fp64")
+        o = make_options(**opts)
+        self.ensure_workspace(workspace_bytes(m, n, **opts))
+        st_ptr = status.data_ptr() if status is not None else None
+        _check(lib().svt_polar_f64(self.handle, ctypes.c_void_p(a_ptr), m, n, lda,
+                                   ctypes.c_float(tau), ctypes.byref(o),
+                                   ctypes.c_void_p(out.data_ptr()), out.stride(0),
+                                   ctypes.c_void_p(st_ptr), ctypes.c_void_p(_stream_ptr(stream))),
+               "svt_polar_f64")
         return out
 
     def prox_grad_step(self, X, M, mask, lam: float, Z=None, step: float = 1.0, status=None,

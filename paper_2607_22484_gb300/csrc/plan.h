@@ -36,6 +36,7 @@ struct Resolved {
     int hp_steps;   // leading S-chain steps in the FP32-class tier (BF16 tier)
     int fuse;       // one persistent launch for all products of a solve
     int tile;       // requested tile-width code (0 automatic); read by svt_polar_ex only
+    int out64 = 0;  // FP64 tier only: the result is stored as FP64 (svt_polar_f64)
 };
 
 bool resolve(const svt_options *in, Resolved *r);
@@ -156,12 +157,13 @@ struct Key {
     size_t ws_base;
     int force_bn;
     int fuse;
+    int out64;
     bool operator<(const Key &o) const
     {
         return std::tie(m, n, iters, prec, schedule, norm, polish, mode, hp_steps, ell0, delta,
-                        ws_base, force_bn, fuse) <
+                        ws_base, force_bn, fuse, out64) <
                std::tie(o.m, o.n, o.iters, o.prec, o.schedule, o.norm, o.polish, o.mode,
-                        o.hp_steps, o.ell0, o.delta, o.ws_base, o.force_bn, o.fuse);
+                        o.hp_steps, o.ell0, o.delta, o.ws_base, o.force_bn, o.fuse, o.out64);
     }
 };
 
@@ -180,6 +182,9 @@ struct CallArgs {
 
 svt_status validate(const float *A, int64_t m, int64_t n, int64_t lda, float tau, const float *Y,
                     int64_t ldy);
+// The same checks for an output of ysz-byte elements (svt_polar_f64: FP64).
+svt_status validate_out(const float *A, int64_t m, int64_t n, int64_t lda, float tau,
+                        const void *Y, int64_t ldy, size_t ysz);
 
 // Whether the byte ranges [a, a + abytes) and [b, b + bbytes) intersect.
 inline bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes)

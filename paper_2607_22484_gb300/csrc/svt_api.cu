@@ -164,6 +164,7 @@ bool resolve(const svt_options *in, Resolved *r)
     if (o.tile != 0 && o.tile != 128 && o.tile != 256 && o.tile != kBnPair)
         return false;
     r->tile = (o.prec == SVT_FP64) ? 0 : o.tile;
+    r->out64 = 0;
     return true;
 }
 
@@ -642,12 +643,13 @@ struct Builder {
             P.kernel_launches += 1;
         }
 
-        // Combine: Y = 1/2 B S' + 1/2 B (FP32 out, transposed back for wide input).
+        // Combine: Y = 1/2 B S' + 1/2 B (FP32 out, or FP64 for svt_polar_f64; transposed
+        // back for wide input).
         {
             Epi e = epi0();
             e.alpha = 0.5;
             set_c(e, L.B, 0.5);
-            e.o_kind = f64 ? O_F32 : O_F32;
+            e.o_kind = (f64 && o.out64) ? O_F64 : O_F32;
             e.o_trans = P.wide ? 1 : 0;
             e.norm_acc = scal(SC_NRM_OUT);
             if (!emit({{&L.B, &L.Sp, M, N, N, false, e, PT_O_IS_Y, 2}}))
@@ -1046,7 +1048,7 @@ svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_
     if (force_bn == 0 && r.fuse && r.prec != SVT_FP64)
         force_bn = fused_auto_width(m, n);
     Key k{m, n, r.iters, r.prec, r.schedule, r.norm, r.polish, r.mode, r.hp_steps, r.ell0, r.delta,
-          ws_base, force_bn, r.fuse};
+          ws_base, force_bn, r.fuse, r.out64};
     auto it = ctx->plans.find(k);
     if (it != ctx->plans.end()) {
         *out = it->second.get();
@@ -1104,21 +1106,25 @@ svt_status plan_status_copy(svt_ctx *ctx, const Plan &P, int *host_dst, cudaStre
 
 static bool finite_tau(float tau) { return std::isfinite(tau) && tau >= 0.0f; }
 
-svt_status validate(const float *A, int64_t m, int64_t n, int64_t lda, float tau, const float *Y,
-                    int64_t ldy)
+svt_status validate_out(const float *A, int64_t m, int64_t n, int64_t lda, float tau,
+                        const void *Y, int64_t ldy, size_t ysz)
 {
     if (!A || !Y || m <= 0 || n <= 0 || lda < n || ldy < n || !finite_tau(tau))
         return SVT_ERR_INVALID;
     if (m > (int64_t)1 << 20 || n > (int64_t)1 << 20)
         return SVT_ERR_UNSUPPORTED;
     // A and Y must not overlap
-    const char *a0 = reinterpret_cast<const char *>(A);
-    const char *a1 = reinterpret_cast<const char *>(A + (m - 1) * lda + n);
-    const char *y0 = reinterpret_cast<const char *>(Y);
-    const char *y1 = reinterpret_cast<const char *>(Y + (m - 1) * ldy + n);
-    if (a0 < y1 && y0 < a1)
+    const size_t abytes = ((size_t)(m - 1) * (size_t)lda + (size_t)n) * sizeof(float);
+    const size_t ybytes = ((size_t)(m - 1) * (size_t)ldy + (size_t)n) * ysz;
+    if (overlaps(A, abytes, Y, ybytes))
         return SVT_ERR_INVALID;
     return SVT_OK;
+}
+
+svt_status validate(const float *A, int64_t m, int64_t n, int64_t lda, float tau, const float *Y,
+                    int64_t ldy)
+{
+    return validate_out(A, m, n, lda, tau, Y, ldy, sizeof(float));
 }
 
 } // namespace svt
@@ -1249,6 +1255,37 @@ svt_status svt_polar_ex(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int
     if (st != SVT_OK)
         return st;
     CallArgs a{A, lda, tau, Y, ldy, d_status};
+    return run_plan(ctx, *plan, a, static_cast<cudaStream_t>(stream));
+}
+
+svt_status svt_polar_f64(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int64_t lda,
+                         float tau, const svt_options *opt, double *Y, int64_t ldy,
+                         svt_status *d_status, void *stream)
+{
+    if (!ctx)
+        return SVT_ERR_INVALID;
+    svt_status st = validate_out(A, m, n, lda, tau, Y, ldy, sizeof(double));
+    if (st != SVT_OK)
+        return st;
+    Resolved r;
+    if ((st = resolve_status(opt, &r)) != SVT_OK)
+        return st;
+    if (r.prec != SVT_FP64)
+        return SVT_ERR_INVALID;  // only the FP64 tier has an FP64 result
+    if (m > kF64MaxDim || n > kF64MaxDim)
+        return SVT_ERR_UNSUPPORTED;
+    r.out64 = 1;
+    if (serve_busy(ctx))
+        return SVT_ERR_BUSY;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    Plan *plan = nullptr;
+    st = get_plan(ctx, m, n, r, 0, ctx->ws_bytes, &plan);
+    if (st != SVT_OK)
+        return st;
+    // The plan's combine stores FP64; the output pointer travels as the call's Y.
+    CallArgs a{A, lda, tau, reinterpret_cast<float *>(Y), ldy, d_status};
     return run_plan(ctx, *plan, a, static_cast<cudaStream_t>(stream));
 }
 

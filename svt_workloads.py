@@ -76,6 +76,23 @@ def marchenko_pastur(m: int, n: int | None = None, seed: int = SEED_MP) -> np.nd
     return (rng.standard_normal((m, n)) * scale).astype(np.float32)
 
 
+def quarter_circle_sigma(n: int) -> np.ndarray:
+    """Singular values of an n x n N(0, 1/n) matrix follow the quarter-circle law on
+    [0, 2] (density sqrt(4 - s^2) / pi, the square case of Marchenko-Pastur); returns
+    its (i - 1/2) / n quantiles, largest first, by bisection on the closed-form
+    distribution function. With Haar singular vectors this gives a matrix shaped like
+    the benchmark's whose SVD, and hence A_tau, is known exactly."""
+    cdf = lambda s: (s * np.sqrt(4.0 - s * s) / 2.0 + 2.0 * np.arcsin(s / 2.0)) / np.pi
+    p = (np.arange(n) + 0.5) / n
+    lo, hi = np.zeros(n), np.full(n, 2.0)
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        below = cdf(mid) < p
+        lo = np.where(below, mid, lo)
+        hi = np.where(below, hi, mid)
+    return np.ascontiguousarray(np.sort(0.5 * (lo + hi))[::-1])
+
+
 def low_rank_plus_noise(m: int, n: int, rank: int, seed: int,
                         sig_lo: float = 1.0, sig_hi: float = 10.0,
                         noise: float = 0.01) -> np.ndarray:

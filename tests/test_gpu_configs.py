@@ -35,7 +35,7 @@ def _known(m, n, seed):
 
 
 @pytest.mark.parametrize("shape", [(8192, 2048), (2048, 8192)])
-def test_rectangular_full_size_and_corollary(ctx, shape):
+def test_rectangular_full_size_and_corollary(ctx, shape, block_spread):
     m, n = shape
     a, q1, sig, q2 = _known(m, n, seed=m + 3 * n)
     tau = 1.0
@@ -47,12 +47,16 @@ def test_rectangular_full_size_and_corollary(ctx, shape):
     exact = (q1[:, keep] * (sig[keep] - tau)) @ q2[:, keep].T
     err = oracle.relerr(y.cpu().numpy(), exact)
     assert err < 2e-2, err
+    # block by block: no part of the output stands out of the rounding noise
+    for b in (32, 128):
+        assert block_spread(y.cpu().numpy() - exact, b) < 2.0, b
     # Corollary 1: tau between sigma_65 (<= 0.5) and sigma_64 (>= 1.5) gives [A]_64
     y = ctx.polar(dev, tau, iters=20, prec="bf16", mode="rank_r")
     torch.cuda.synchronize()
     best = (q1[:, keep] * sig[keep]) @ q2[:, keep].T
     err = oracle.relerr(y.cpu().numpy(), best)
     assert err < 2e-2, err
+    assert block_spread(y.cpu().numpy() - best, 128) < 2.0
 
 
 def test_error_curves_marchenko_pastur(ctx):
@@ -103,18 +107,7 @@ def test_error_curves_marchenko_pastur(ctx):
 
 
 def _quarter_circle_quantiles(n):
-    """Singular values of an n x n N(0, 1/n) matrix follow the quarter-circle law
-    on [0, 2] (density sqrt(4 - s^2) / pi); returns its (i - 1/2) / n quantiles,
-    largest first, by bisection on the closed-form distribution function."""
-    cdf = lambda s: (s * np.sqrt(4.0 - s * s) / 2.0 + 2.0 * np.arcsin(s / 2.0)) / np.pi
-    p = (np.arange(n) + 0.5) / n
-    lo, hi = np.zeros(n), np.full(n, 2.0)
-    for _ in range(60):
-        mid = 0.5 * (lo + hi)
-        below = cdf(mid) < p
-        lo = np.where(below, mid, lo)
-        hi = np.where(below, hi, mid)
-    return np.ascontiguousarray(np.sort(0.5 * (lo + hi))[::-1])
+    return wl.quarter_circle_sigma(n)
 
 
 def test_error_curves_mp4096_known_spectrum(ctx):
