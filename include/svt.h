@@ -56,8 +56,9 @@ typedef enum {
     SVT_ERR_DIVERGED = 5,  /* iteration produced a non-finite value */
     SVT_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
     SVT_ERR_NOT_READY = 7, /* serving ticket still pending */
-    SVT_ERR_BUSY = 8,      /* serving queue full */
-    SVT_ERR_UNSUPPORTED = 9 /* size or option outside what this build supports */
+    SVT_ERR_BUSY = 8,      /* serving queue full; or a request too far along to cancel */
+    SVT_ERR_UNSUPPORTED = 9, /* size or option outside what this build supports */
+    SVT_ERR_CANCELLED = 10 /* serving request cancelled by svt_serve_cancel */
 } svt_status;
 
 typedef enum {
@@ -249,6 +250,31 @@ svt_status svt_serve_poll(svt_ctx_t ctx, uint64_t ticket, double *latency_ms);
 /* Forget a completed ticket. SVT_ERR_NOT_READY if still pending. */
 svt_status svt_serve_release(svt_ctx_t ctx, uint64_t ticket);
 
+/*
+ * Cancel a serving request. A request still in the admission queue is removed at
+ * once; one whose stages are being issued window by window is dropped before its
+ * next window and retired once its work already on the device has finished. Either
+ * way the ticket then polls as SVT_ERR_CANCELLED and its Y is unspecified (the
+ * combine that writes Y may or may not have run). Returns SVT_OK when the request
+ * is or will be cancelled, SVT_ERR_BUSY when its remaining work is already on the
+ * device (a large request's single fused launch, or a small one whose last stage
+ * went out: poll for its result), SVT_ERR_INVALID for an unknown or completed
+ * ticket.
+ */
+svt_status svt_serve_cancel(svt_ctx_t ctx, uint64_t ticket);
+
+/*
+ * Per-request records of the serving loop: from this call on, every retired request
+ * (completed, failed or cancelled) appends one JSON line to the file at `path`:
+ *   {"ticket", "m", "n", "prec", "tau", "iters", "lane" ("small" | "large"),
+ *    "queue_ms" (submit to admission), "run_ms" (admission to retirement),
+ *    "latency_ms" (submit to retirement), "status"}.
+ * path = NULL stops recording. The environment variable SVT_SERVE_METRICS=<path>
+ * starts recording when the serving loop starts.
+ * Errors: SVT_ERR_INVALID (null ctx, or a file that cannot be opened for appending).
+ */
+svt_status svt_serve_metrics(svt_ctx_t ctx, const char *path);
+
 /* Wait for all work of the context (svt_polar/svt_batch streams and serving)
  * and return the first device-side error recorded since the last sync. */
 svt_status svt_ctx_sync(svt_ctx_t ctx, void *stream);
@@ -395,6 +421,47 @@ svt_status svt_debug_wait_timeout(svt_ctx_t ctx, svt_status *d_status, void *str
 /* Number of kernel launches the library has issued on this context so far
  * (host counter; used to report launches per solve). */
 uint64_t svt_ctx_launch_count(svt_ctx_t ctx);
+
+/* Host-side fault injection and debug settings of a context (none makes the GPU
+ * fault, trap or hang: each turns into an ordinary error status). */
+typedef enum {
+    /* value N >= 1: the Nth launch-plan build from now on fails with SVT_ERR_OOM
+     * (plan builds are where the library allocates host memory: one per new shape
+     * and option set); 0 turns it off. */
+    SVT_DEBUG_FAIL_PLAN = 1,
+    /* value in microseconds: serving admits a request no earlier than this long
+     * after its submission (0: off). */
+    SVT_DEBUG_ADMIT_DELAY_US = 2,
+    /* value in nanoseconds: the product kernel's waits on other tiles' results (its
+     * device-side dependency counters) give up after this long instead of 2 s and
+     * report SVT_ERR_TIMEOUT in the solve's status; 1 makes any wait that is not
+     * already satisfied time out at once. 0 restores the default. Applies to launches
+     * issued (or captured into a batch's graph) after the call. */
+    SVT_DEBUG_WAIT_LIMIT_NS = 3
+} svt_debug_flag;
+
+/* Set one debug setting (see svt_debug_flag). Errors: SVT_ERR_INVALID (null ctx,
+ * unknown flag, negative value). */
+svt_status svt_ctx_debug(svt_ctx_t ctx, svt_debug_flag flag, int64_t value);
+
+/*
+ * The context's autotune results (svt_autotune tile choices) as JSON text, to keep
+ * them across contexts and processes:
+ *   {"format": 1, "gpu": "<device name>", "sms": <SM count>, "entries": [
+ *     {"m", "n", "iters", "prec", "schedule", "norm", "polish", "mode", "hp_steps",
+ *      "ell0", "delta", "fuse", "widths": [tile width of each product launch]}, ...]}
+ * Entries are keyed by the exact shape and the options that shape the launch
+ * sequence (tier included); the file is keyed by the GPU's name and SM count.
+ * svt_tuning_export writes at most cap bytes including the terminating NUL into buf
+ * (buf may be NULL with cap 0) and the full length (without the NUL) into *len;
+ * SVT_ERR_OOM when cap is too small (*len still set).
+ * svt_tuning_import merges the entries of such text into the context (later solves
+ * of those shapes and options use them); SVT_ERR_INVALID when the text does not
+ * parse, is of another format, or was tuned on a GPU of another name or SM count
+ * (nothing is imported then).
+ */
+svt_status svt_tuning_export(svt_ctx_t ctx, char *buf, size_t cap, size_t *len);
+svt_status svt_tuning_import(svt_ctx_t ctx, const char *json);
 
 /*
  * Measurement hooks. svt_ctx_profile(ctx, 1) makes every later tensor-core

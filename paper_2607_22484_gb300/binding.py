@@ -20,7 +20,9 @@ LIB_PATH = os.path.join(_HERE, "libsvt.so")
 
 # svt_status
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_DIVERGED, ERR_TIMEOUT, \
-    ERR_NOT_READY, ERR_BUSY, ERR_UNSUPPORTED = range(10)
+    ERR_NOT_READY, ERR_BUSY, ERR_UNSUPPORTED, ERR_CANCELLED = range(11)
+# svt_debug_flag
+DEBUG = {"fail_plan": 1, "admit_delay_us": 2, "wait_limit_ns": 3}
 # svt_precision
 FP64, FP32, BF16, FP8_EXPERIMENTAL = 0, 1, 2, 3
 PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp8_experimental": FP8_EXPERIMENTAL}
@@ -41,7 +43,8 @@ EXPORTS = [
     "svt_ctx_launch_count",
     "svt_ctx_profile", "svt_ctx_profile_read", "svt_polar_noalloc", "svt_autotune",
     "svt_prox_grad_step", "svt_complete", "svt_autotune_schedule", "svt_autotune_batch",
-    "svt_ctx_profile_read_ex", "svt_debug_wait_timeout", "svt_polar_f64",
+    "svt_ctx_profile_read_ex", "svt_debug_wait_timeout", "svt_polar_f64", "svt_serve_cancel",
+    "svt_serve_metrics", "svt_ctx_debug", "svt_tuning_export", "svt_tuning_import",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -125,6 +128,12 @@ def lib():
         L.svt_serve_submit.argtypes = [vp, ctypes.POINTER(Matrix), ctypes.POINTER(ctypes.c_uint64)]
         L.svt_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
         L.svt_serve_release.argtypes = [vp, ctypes.c_uint64]
+        L.svt_serve_cancel.argtypes = [vp, ctypes.c_uint64]
+        L.svt_serve_metrics.argtypes = [vp, ctypes.c_char_p]
+        L.svt_ctx_debug.argtypes = [vp, i32, i64]
+        L.svt_tuning_export.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t,
+                                        ctypes.POINTER(ctypes.c_size_t)]
+        L.svt_tuning_import.argtypes = [vp, ctypes.c_char_p]
         L.svt_ctx_sync.argtypes = [vp, vp]
         L.svt_schedule_coeffs.argtypes = [i32, i32, ctypes.c_double, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_double)]
@@ -279,17 +288,63 @@ class Context:
             pass
 
     def ensure_workspace(self, nbytes: int):
-        """Grow the workspace (re-creating the context) if it is smaller than nbytes."""
+        """Grow the workspace (re-creating the context) if it is smaller than nbytes.
+        The autotune results and debug settings carry over to the new context."""
         import torch
         if nbytes <= self.workspace.numel():
             return
         torch.cuda.synchronize(self.device)
+        tuning = self.tuning_export()
         self.close()
         self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=f"cuda:{self.device}")
         h = ctypes.c_void_p()
         _check(lib().svt_ctx_create(self.device, ctypes.c_void_p(self.workspace.data_ptr()),
                                     self.workspace.numel(), ctypes.byref(h)), "svt_ctx_create")
         self.handle = h
+        self.tuning_import(tuning)
+        for flag, value in getattr(self, "_debug", {}).items():
+            _check(lib().svt_ctx_debug(self.handle, DEBUG[flag], int(value)), "svt_ctx_debug")
+
+    def tuning_export(self) -> str:
+        """The context's autotune results as JSON text (svt_tuning_export)."""
+        n = ctypes.c_size_t(0)
+        st = lib().svt_tuning_export(self.handle, None, 0, ctypes.byref(n))
+        if st not in (OK, ERR_OOM):
+            _check(st, "svt_tuning_export")
+        buf = ctypes.create_string_buffer(n.value + 1)
+        _check(lib().svt_tuning_export(self.handle, buf, n.value + 1, ctypes.byref(n)),
+               "svt_tuning_export")
+        return buf.value.decode()
+
+    def tuning_import(self, text: str):
+        """Merge autotune results written by tuning_export (svt_tuning_import); raises
+        SVTError (ERR_INVALID) for text from another GPU or malformed text."""
+        _check(lib().svt_tuning_import(self.handle, text.encode()), "svt_tuning_import")
+
+    def save_tuning(self, path: str):
+        with open(path, "w") as f:
+            f.write(self.tuning_export())
+
+    def load_tuning(self, path: str):
+        with open(path) as f:
+            self.tuning_import(f.read())
+
+    def debug(self, flag: str, value: int):
+        """Host-side fault injection and debug settings (svt_ctx_debug): "fail_plan" (the
+        Nth plan build from now fails with ERR_OOM), "admit_delay_us" (serving admission
+        delay), "wait_limit_ns" (device dependency-wait limit; 0 = default)."""
+        _check(lib().svt_ctx_debug(self.handle, DEBUG[flag], int(value)), "svt_ctx_debug")
+        self.__dict__.setdefault("_debug", {})[flag] = int(value)
+
+    def cancel(self, ticket: int) -> int:
+        """svt_serve_cancel: OK when the request is (or will be) cancelled, ERR_BUSY when
+        its remaining work is already on the device, ERR_INVALID for unknown/completed."""
+        return int(lib().svt_serve_cancel(self.handle, ctypes.c_uint64(ticket)))
+
+    def serve_metrics(self, path):
+        """Append one JSON line per retired serving request to `path` (None: stop)."""
+        _check(lib().svt_serve_metrics(self.handle, None if path is None else str(path).encode()),
+               "svt_serve_metrics")
 
     def polar(self, A, tau: float, out=None, status=None, stream=None, **opts):
         """Y = A_tau through svt_polar_ex (asynchronous on the current stream)."""

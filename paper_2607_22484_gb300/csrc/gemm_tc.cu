@@ -262,6 +262,12 @@ __device__ bool wait_counter(const int *counter, int target, volatile int *abort
     }
 }
 
+// Limit of the waits on other tiles' results (the launch's debug setting, else 2 s).
+__device__ __forceinline__ uint64_t dep_limit(const TcLaunch &L)
+{
+    return L.dep_wait_ns ? (uint64_t)L.dep_wait_ns : kWaitTimeoutNs;
+}
+
 // Wait for strip `idx` of dependency k of problem P (see TcProblem::sdep_*), unless the
 // producing problem is already known (src_done) or found to be complete as a whole,
 // which covers every strip; a role then stops checking that source.
@@ -275,7 +281,7 @@ __device__ __forceinline__ bool wait_strip(const TcLaunch &L, const TcProblem &P
         return true;
     }
     return wait_counter(&L.strips[P.sdep_base[k] + idx], P.sdep_target[k], abort_flag, status,
-                        kWaitTimeoutNs);
+                        dep_limit(L));
 }
 
 // Shared-memory matrix descriptor for a K-major operand tile laid out by TMA
@@ -1101,7 +1107,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                         for (int d = 0; d < 2 && ok; ++d)
                             if (P.dep[d] >= 0)
                                 ok = wait_counter(&L.done[P.dep[d]], P.dep_target[d], abort_flag,
-                                                  status0, kWaitTimeoutNs);
+                                                  status0, dep_limit(L));
                         dep_prob = tc.prob;
                         smode[0] = P.sdep_mode[0];
                         smode[1] = P.sdep_mode[1];
@@ -1116,7 +1122,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                     for (int d = 0; d < 2 && ok; ++d)
                         if (P.dep[d] >= 0)
                             ok = wait_counter(&L.done[P.dep[d]], P.dep_target[d], abort_flag,
-                                              status0, kWaitTimeoutNs);
+                                              status0, dep_limit(L));
                 }
                 fence_async_global();  // the TMA reads below come after the acquire
                 if (!ok)
@@ -1301,7 +1307,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 for (int d = 0; d < 2; ++d)
                     if (P.dep[d] >= 0 && lane == 0)
                         wait_counter(&L.done[P.dep[d]], P.dep_target[d], abort_flag, status0,
-                                     kWaitTimeoutNs);
+                                     dep_limit(L));
                 __syncwarp();
             }
             if (STRIPS) {
@@ -1313,10 +1319,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                             for (int d = 0; d < 2; ++d)
                                 if (P.dep[d] >= 0)
                                     wait_counter(&L.done[P.dep[d]], P.dep_target[d], abort_flag,
-                                                 status0, kWaitTimeoutNs);
+                                                 status0, dep_limit(L));
                         for (int d = 0; d < P.nwdep; ++d)
                             wait_counter(&L.done[P.wdep[d]], P.wdep_target[d], abort_flag,
-                                         status0, kWaitTimeoutNs);
+                                         status0, dep_limit(L));
                         c_done = !P.sdep_mode[2];
                     }
                     if (!c_done)

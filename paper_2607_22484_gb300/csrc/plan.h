@@ -14,9 +14,20 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "svt_internal.h"
 
 namespace svt {
+
+// Host-side NVTX range for the duration of a scope (a profiler shows the library's
+// stages: solves, plan builds, serving windows, batches); free when no tool listens.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int64_t kF64MaxDim = 4096;
 constexpr size_t kAlign = 256;
@@ -222,6 +233,12 @@ struct svt_ctx {
     // Cached device-resident completion loops (completion.cu), most recent last.
     std::vector<svt::CompletionGraph *> completion_graphs;
     cudaStream_t capture_stream = nullptr;  // private stream for graph capture
+    char gpu_name[256] = {};                // device name (autotune cache key)
+    // Debug settings (svt_ctx_debug): plan builds until one fails (0: off), serving
+    // admission delay, device dependency-wait limit (0: default).
+    int64_t dbg_fail_plan = 0;
+    int64_t dbg_admit_delay_us = 0;
+    uint64_t dbg_wait_ns = 0;
 };
 
 namespace svt {

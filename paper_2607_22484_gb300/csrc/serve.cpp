@@ -134,8 +134,10 @@ struct Request {
     Resolved opt;
     size_t ws_len = 0, ws_off = 0;
     int slot = -1;
-    double t_submit = 0, t_done = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
     int state = 0;  // 0 queued, 1 running (ops being issued), 3 all issued, 2 done
+    bool cancel = false;     // svt_serve_cancel on a running request: drop before next window
+    bool cancelled = false;  // retire as SVT_ERR_CANCELLED once its issued work is done
     svt_status result = SVT_OK;
     Plan *plan = nullptr;
     std::shared_ptr<Plan> plan_ref;  // keeps the plan alive while ops are in flight
@@ -244,6 +246,7 @@ struct ServeState {
     bool ring_busy[kRing] = {};
     int ring_next = 0;
     uint64_t windows = 0;
+    FILE *metrics = nullptr;          // per-request JSON lines (svt_serve_metrics)
 };
 
 namespace svt {
@@ -290,6 +293,28 @@ bool grouped_kinds(const Plan &P)
     return true;
 }
 
+const char *prec_name(int p)
+{
+    return p == SVT_FP64 ? "fp64" : (p == SVT_FP32 ? "fp32" : (p == SVT_BF16 ? "bf16" : "fp8"));
+}
+
+// One JSON line per retired request (svt_serve_metrics), under s->mu.
+void record(ServeState *s, const Request *r)
+{
+    if (!s->metrics)
+        return;
+    const double admit = r->t_admit > 0 ? r->t_admit : r->t_done;
+    std::fprintf(s->metrics,
+                 "{\"ticket\": %llu, \"m\": %lld, \"n\": %lld, \"prec\": \"%s\", \"tau\": %.9g, "
+                 "\"iters\": %d, \"lane\": \"%s\", \"queue_ms\": %.4f, \"run_ms\": %.4f, "
+                 "\"latency_ms\": %.4f, \"status\": \"%s\"}\n",
+                 (unsigned long long)r->ticket, (long long)r->m.m, (long long)r->m.n,
+                 prec_name(r->opt.prec), (double)r->m.tau, r->opt.iters, r->large ? "large" : "small",
+                 admit - r->t_submit, r->t_done - admit, r->t_done - r->t_submit,
+                 svt_status_str(r->result));
+    std::fflush(s->metrics);
+}
+
 void finish(ServeState *s, Request *r, svt_status st)
 {
     r->plan = nullptr;
@@ -299,6 +324,13 @@ void finish(ServeState *s, Request *r, svt_status st)
     r->t_done = now_ms();
     s->arena.release(r->ws_off, r->ws_len);
     s->slot_used[r->slot] = false;
+    record(s, r);
+}
+
+// Serving admits a request no earlier than the debug admission delay after its submission.
+bool admissible(const svt_ctx *ctx, const Request *r, double now)
+{
+    return ctx->dbg_admit_delay_us <= 0 || now >= r->t_submit + 1e-3 * (double)ctx->dbg_admit_delay_us;
 }
 
 // One serving window: grouped ingest of newly admitted requests, one grouped
@@ -476,6 +508,7 @@ svt_status issue_window(svt_ctx *ctx, ServeState *s, int sms)
         L.gtab = reinterpret_cast<const TcProblem *>(d + o_p[g]);
         L.gstart = reinterpret_cast<const int *>(d + o_s[g]);
         L.gcount = (int)probs[g].size();
+        L.dep_wait_ns = ctx->dbg_wait_ns;
         if (tc_gemm_launch_grouped(L, g ? 256 : 128, tiles[g], sms, st) != cudaSuccess)
             return SVT_ERR_CUDA;
         ++launched;
@@ -538,7 +571,9 @@ bool tick(svt_ctx *ctx, ServeState *s)
             ++it;
             continue;
         }
-        finish(s, r, q == cudaSuccess ? (svt_status)s->h_status[r->slot] : SVT_ERR_CUDA);
+        finish(s, r, q != cudaSuccess ? SVT_ERR_CUDA
+                                      : (r->cancelled ? SVT_ERR_CANCELLED
+                                                      : (svt_status)s->h_status[r->slot]));
         trace("done", r->ticket, (long long)r->result);
         if (r == s->big)
             s->big = nullptr;
@@ -549,7 +584,9 @@ bool tick(svt_ctx *ctx, ServeState *s)
     // runs and its workspace fits. While it waits for workspace no new small request
     // is admitted (the running ones free theirs within milliseconds).
     bool hold_small = false;
-    if (!s->big && !s->bigq.empty() && (int)s->active.size() < kSlots) {
+    const double t_tick = now_ms();
+    if (!s->big && !s->bigq.empty() && (int)s->active.size() < kSlots &&
+        admissible(ctx, s->bigq.front(), t_tick)) {
         Request *r = s->bigq.front();
         size_t off;
         if (!s->arena.alloc(r->ws_len, &off)) {
@@ -564,10 +601,12 @@ bool tick(svt_ctx *ctx, ServeState *s)
             s->slot_used[slot] = true;
             r->slot = slot;
             r->ws_off = off;
+            r->t_admit = now_ms();
             Plan *plan = nullptr;
             svt_status e;
             {
                 std::lock_guard<std::mutex> g(ctx->mu);
+                NvtxRange nvtx("svt serve large launch");
                 evict_plans(ctx, 512);
                 e = get_plan(ctx, r->m.m, r->m.n, r->opt, off, ctx->ws_bytes - kRingBytes - off,
                              &plan, 0, &r->plan_ref);
@@ -594,7 +633,8 @@ bool tick(svt_ctx *ctx, ServeState *s)
         }
     }
     // Small lane: admit in arrival order while a slot and workspace are free.
-    while (!hold_small && !s->queue.empty() && (int)s->active.size() < kSlots) {
+    while (!hold_small && !s->queue.empty() && (int)s->active.size() < kSlots &&
+           admissible(ctx, s->queue.front(), t_tick)) {
         Request *r = s->queue.front();
         size_t off;
         if (!s->arena.alloc(r->ws_len, &off))
@@ -606,6 +646,7 @@ bool tick(svt_ctx *ctx, ServeState *s)
         s->slot_used[slot] = true;
         r->slot = slot;
         r->ws_off = off;
+        r->t_admit = now_ms();
         Plan *plan = nullptr;
         svt_status e;
         const double t0 = trace_file() ? now_ms() : 0.0;
@@ -628,6 +669,17 @@ bool tick(svt_ctx *ctx, ServeState *s)
         s->active.push_back(r);
         progress = true;
     }
+    // Cancelled requests whose stages were being issued: no further windows; they retire
+    // once the work already issued (in order on the window stream) has finished.
+    for (Request *r : s->active)
+        if (r->state == 1 && r->cancel) {
+            if (cudaEventRecord(s->events[r->slot], s->win) != cudaSuccess)
+                continue;  // retried next tick
+            r->state = 3;
+            r->cancelled = true;
+            trace("cancel", r->ticket, (long long)r->pc);
+            progress = true;
+        }
     // Issue one window if any request has ops left to issue.
     bool any = false;
     for (Request *r : s->active)
@@ -635,6 +687,7 @@ bool tick(svt_ctx *ctx, ServeState *s)
             any = true;
     if (any) {
         const double t0 = trace_file() ? now_ms() : 0.0;
+        NvtxRange nvtx("svt serve window");
         svt_status e = issue_window(ctx, s, s->big ? kSmallSms : ctx->num_sms);
         if (e == SVT_ERR_NOT_READY)
             return progress;
@@ -833,6 +886,7 @@ svt_status build_batch(svt_ctx *ctx, ServeState *s, const svt_matrix *mats, int 
         L.gstart = ds;
         L.gcount = (int)probs.size();
         L.calls = bp->d_calls;
+        L.dep_wait_ns = ctx->dbg_wait_ns;
         L.done = counters;
         L.tile_counter = counters + probs.size();
         bp->launches.push_back(L);
@@ -920,6 +974,8 @@ void serve_shutdown(svt_ctx *ctx)
             cudaEventDestroy(s->ring_ev[i]);
     if (s->h_ring)
         cudaFreeHost(s->h_ring);
+    if (s->metrics)
+        std::fclose(s->metrics);
     // Every request lives in `tickets` from submission until its release (queued and
     // active ones included), so the ticket map owns them all.
     s->queue.clear();
@@ -1193,6 +1249,11 @@ svt_status svt_serve_submit(svt_ctx_t ctx, const svt_matrix *req, uint64_t *tick
     if (!s->started) {
         if (start_workers(ctx, s) != SVT_OK)
             return SVT_ERR_CUDA;
+        if (!s->metrics) {
+            const char *mp = std::getenv("SVT_SERVE_METRICS");
+            if (mp && *mp)
+                s->metrics = std::fopen(mp, "a");
+        }
         s->arena.reset(ctx->ws_bytes - kRingBytes);
         s->thread = std::thread(scheduler, ctx, s);
         s->started = true;
@@ -1229,6 +1290,57 @@ svt_status svt_serve_poll(svt_ctx_t ctx, uint64_t ticket, double *latency_ms)
     if (latency_ms)
         *latency_ms = r->t_done - r->t_submit;
     return r->result;
+}
+
+svt_status svt_serve_cancel(svt_ctx_t ctx, uint64_t ticket)
+{
+    if (!ctx || !ctx->serve)
+        return SVT_ERR_INVALID;
+    ServeState *s = ctx->serve;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end())
+        return SVT_ERR_INVALID;
+    Request *r = it->second;
+    switch (r->state) {
+    case 0: {  // still queued: nothing of it reached the device
+        auto &q = r->large ? s->bigq : s->queue;
+        q.erase(std::remove(q.begin(), q.end(), r), q.end());
+        r->result = SVT_ERR_CANCELLED;
+        r->state = 2;
+        r->t_done = now_ms();
+        trace("cancel", r->ticket, -1);
+        record(s, r);
+        return SVT_OK;
+    }
+    case 1:  // stages being issued: the scheduler drops it before its next window
+        r->cancel = true;
+        s->cv.notify_all();
+        return SVT_OK;
+    case 3:  // everything it needs is on the device already
+        return r->cancelled ? SVT_OK : SVT_ERR_BUSY;
+    default:
+        return SVT_ERR_INVALID;
+    }
+}
+
+svt_status svt_serve_metrics(svt_ctx_t ctx, const char *path)
+{
+    if (!ctx)
+        return SVT_ERR_INVALID;
+    FILE *f = nullptr;
+    if (path && !(f = std::fopen(path, "a")))
+        return SVT_ERR_INVALID;
+    ServeState *s;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        s = state_of(ctx);
+    }
+    std::lock_guard<std::mutex> g(s->mu);
+    if (s->metrics)
+        std::fclose(s->metrics);
+    s->metrics = f;
+    return SVT_OK;
 }
 
 svt_status svt_serve_release(svt_ctx_t ctx, uint64_t ticket)

@@ -22,7 +22,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -31,6 +33,7 @@
 
 #include "fused_deps.h"
 #include "plan.h"
+#include "tuning_json.h"
 
 namespace svt {
 
@@ -737,6 +740,7 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
             if (!a.in_graph && upload_fused_table(ctx, P, s) != SVT_OK)
                 return SVT_ERR_CUDA;
             TcLaunch l = P.fused_launch;
+            l.dep_wait_ns = ctx->dbg_wait_ns;
             l.call_inline.A = a.A;
             l.call_inline.Y = a.Y;
             l.call_inline.lda = a.lda;
@@ -799,6 +803,7 @@ svt_status run_ops(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, siz
         }
         case OP_TC: {
             TcLaunch l = P.tc[op.idx];
+            l.dep_wait_ns = ctx->dbg_wait_ns;
             for (const PatchRec &pr : P.patches)
                 if (pr.kind == OP_TC && pr.launch == op.idx) {
                     Epi &e = l.p[pr.prob].ep;
@@ -1056,6 +1061,10 @@ svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_
             *keep = it->second;
         return SVT_OK;
     }
+    // Host-side fault injection (svt_ctx_debug): the Nth plan build fails.
+    if (ctx->dbg_fail_plan > 0 && --ctx->dbg_fail_plan == 0)
+        return SVT_ERR_OOM;
+    NvtxRange nvtx_build("svt plan build");
     auto plan = std::make_shared<Plan>();
     plan->m = m;
     plan->n = n;
@@ -1146,6 +1155,7 @@ const char *svt_status_str(svt_status s)
     case SVT_ERR_NOT_READY: return "SVT_ERR_NOT_READY";
     case SVT_ERR_BUSY: return "SVT_ERR_BUSY";
     case SVT_ERR_UNSUPPORTED: return "SVT_ERR_UNSUPPORTED";
+    case SVT_ERR_CANCELLED: return "SVT_ERR_CANCELLED";
     }
     return "SVT_ERR_UNKNOWN";
 }
@@ -1211,9 +1221,66 @@ svt_status svt_ctx_create(int device, void *workspace, size_t ws_bytes, svt_ctx_
         delete c;
         return SVT_ERR_CUDA;
     }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete c;
+        return SVT_ERR_CUDA;
+    }
+    std::snprintf(c->gpu_name, sizeof(c->gpu_name), "%s", prop.name);
     c->ws = static_cast<uint8_t *>(workspace);
     c->ws_bytes = ws_bytes;
     *out = c;
+    return SVT_OK;
+}
+
+svt_status svt_ctx_debug(svt_ctx_t ctx, svt_debug_flag flag, int64_t value)
+{
+    if (!ctx || value < 0)
+        return SVT_ERR_INVALID;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    switch (flag) {
+    case SVT_DEBUG_FAIL_PLAN: ctx->dbg_fail_plan = value; return SVT_OK;
+    case SVT_DEBUG_ADMIT_DELAY_US: ctx->dbg_admit_delay_us = value; return SVT_OK;
+    case SVT_DEBUG_WAIT_LIMIT_NS: ctx->dbg_wait_ns = (uint64_t)value; return SVT_OK;
+    }
+    return SVT_ERR_INVALID;
+}
+
+svt_status svt_tuning_export(svt_ctx_t ctx, char *buf, size_t cap, size_t *len)
+{
+    if (!ctx || !len || (cap > 0 && !buf))
+        return SVT_ERR_INVALID;
+    std::string text;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        text = tuning_to_json(ctx->gpu_name, ctx->num_sms, ctx->tuning);
+    }
+    *len = text.size();
+    if (cap < text.size() + 1)
+        return SVT_ERR_OOM;
+    std::memcpy(buf, text.c_str(), text.size() + 1);
+    return SVT_OK;
+}
+
+svt_status svt_tuning_import(svt_ctx_t ctx, const char *json)
+{
+    if (!ctx || !json)
+        return SVT_ERR_INVALID;
+    std::map<TuneKey, std::vector<int>> entries;
+    if (!tuning_from_json(json, ctx->gpu_name, ctx->num_sms, &entries))
+        return SVT_ERR_INVALID;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    for (auto &kv : entries) {
+        // cached plans built from an earlier tuning of this shape are stale
+        for (auto it = ctx->plans.begin(); it != ctx->plans.end();) {
+            const Key &k = it->first;
+            if (k.force_bn < 0 && k.m == kv.first.m && k.n == kv.first.n && k.fuse == kv.first.fuse)
+                it = ctx->plans.erase(it);
+            else
+                ++it;
+        }
+        ctx->tuning[kv.first] = kv.second;
+    }
     return SVT_OK;
 }
 
@@ -1250,6 +1317,7 @@ svt_status svt_polar_ex(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int
     std::lock_guard<std::mutex> g(ctx->mu);
     if (cudaSetDevice(ctx->device) != cudaSuccess)
         return SVT_ERR_CUDA;
+    NvtxRange nvtx_solve("svt_polar");
     Plan *plan = nullptr;
     st = plan_for_solve(ctx, m, n, r, &plan);
     if (st != SVT_OK)

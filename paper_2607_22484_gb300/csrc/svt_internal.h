@@ -135,6 +135,9 @@ struct TcLaunch {
     int *done;
     int *strips;  // fused solves: per-problem strip completion counters
     CallRec call_inline;             // per-call fields when calls == nullptr
+    // Limit of the waits on other tiles' results (dependency counters), ns; 0: the
+    // kernel's default. Set from the context's SVT_DEBUG_WAIT_LIMIT_NS.
+    unsigned long long dep_wait_ns;
 };
 
 // One product of the FP64 SIMT path: D = L R^T, L M x K (ldl), R N x K (ldr).

@@ -45,8 +45,13 @@ def test_batch_recipe_full_range_matches_oracle(block_spread):
     log-uniform 128-1024, aspect 1, 2 and 1/2, rank 5-50 signal + 0.01 noise, tau at the
     noise edge + 0.5) in one svt_batch call, BF16 tier, 20 steps. Every matrix whose tau
     lies at least 5 % of sigma_max from its spectrum is within 2e-2 of Eq. 1 by
-    definition (the oracle); on matrices from 512 up the error is also spread evenly
-    over 64 x 64 blocks (a partly wrong tile would stand out)."""
+    definition (the oracle). Every matrix also equals its single solve (svt_polar_ex: a
+    fused launch with other tiles) to 1e-5, so no tile of the grouped launch can be
+    partly wrong (one wrong 32 x 32 block of a 1024^2 result would differ by ~3e-2).
+    The error against the oracle is spread over 64 x 64 blocks within 3x the RMS block:
+    these low-rank errors are less even than the high-rank ones of the full-size tests
+    (a tiling-free CPU emulation of the BF16 tier on the same matrices from 512 up
+    spreads up to 1.89, on a rank-8 325 x 650 matrix)."""
     items = wl.batch_recipe(256)
     ctx = pkg.Context(0, workspace_bytes=1 << 20)
     As = [torch.from_numpy(it.matrix()).cuda() for it in items]
@@ -56,11 +61,14 @@ def test_batch_recipe_full_range_matches_oracle(block_spread):
                      opts={"iters": 20, "prec": "bf16"})
     torch.cuda.synchronize()
     assert st.cpu().tolist() == [0] * len(items)
-    bound, errs, spreads = 0, [], []
-    for it, y in zip(items, outs):
+    single = pkg.Context(0, workspace_bytes=1 << 20)
+    bound, errs, spreads, vs_single = 0, [], [], []
+    for it, a_dev, y in zip(items, As, outs):
+        ref = single.polar(a_dev, it.tau, iters=20, prec="bf16")
         a = it.matrix().astype(np.float64)
         exact, (u, s, v) = oracle.svt_definition(a, it.tau, return_svd=True)
         got = y.cpu().numpy().astype(np.float64)
+        vs_single.append(oracle.relerr(got, ref.cpu().numpy().astype(np.float64)))
         err = oracle.relerr(got, exact, a)
         if oracle.gap(s, it.tau) >= 0.05:
             bound += 1
@@ -69,10 +77,12 @@ def test_batch_recipe_full_range_matches_oracle(block_spread):
         if max(it.m, it.n) >= 512:
             spreads.append(block_spread(got - exact, 64))
     print(f"batch recipe: {bound} of {len(items)} matrices bind the 2e-2 rule; relerr "
-          f"max {max(errs):.3e} mean {np.mean(errs):.3e}; 64 x 64 block spread max "
-          f"{max(spreads):.3f} over {len(spreads)} matrices from 512 up")
+          f"max {max(errs):.3e} mean {np.mean(errs):.3e}; vs single solves max "
+          f"{max(vs_single):.2e}; 64 x 64 block spread max {max(spreads):.3f} over "
+          f"{len(spreads)} matrices from 512 up")
     assert bound >= len(items) // 2  # the recipe puts tau outside the noise bulk
-    assert max(spreads) < 2.0
+    assert max(vs_single) < 1e-5
+    assert max(spreads) < 3.0
 
 
 def test_batch_tile_option_and_autotune():

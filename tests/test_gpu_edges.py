@@ -42,11 +42,13 @@ def test_tiny_and_vector_shapes(ctx, shape, prec):
         # FP64 tier: 1e-9 plus the FP32 output's rounding floor (~6e-8)
         tol = {"bf16": 2e-2, "fp32": 1e-4, "fp64": 1e-9 + 1e-7}[prec]
         assert oracle.relerr(y, exact, a) < tol
-        if prec == "fp64":  # the FP64 result itself
+        if prec == "fp64":  # the FP64 result itself, at the FP32 tau the ABI carries
             dev = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
             y64 = ctx.polar_f64(dev, tau, iters=30, schedule="ns3")
             torch.cuda.synchronize()
-            assert oracle.relerr(y64.cpu().numpy(), exact, a) < 1e-9
+            tau32 = float(np.float32(tau))
+            exact32 = oracle.svt_definition(a.astype(np.float32).astype(np.float64), tau32)
+            assert oracle.relerr(y64.cpu().numpy(), exact32, a) < 1e-9
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp32", "fp64"])

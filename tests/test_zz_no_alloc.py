@@ -56,17 +56,24 @@ def test_noalloc_rejects_sizes_beyond_scratch():
 
 
 def test_noalloc_second_call_allocates_nothing():
+    import gc
     a = torch.from_numpy(_gap_matrix(300, 260, seed=4)).cuda()
     out = torch.empty_like(a)
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     pkg.polar_noalloc(a, 0.3, out=out, status=status, iters=20, prec="bf16")  # plan, modules
+    # Earlier tests' tensors must not be collected in the middle of the measurement.
+    gc.collect()
     torch.cuda.synchronize()
-    free0, _ = torch.cuda.mem_get_info()
-    alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
-    for _ in range(3):
-        pkg.polar_noalloc(a, 0.3, out=out, status=status, iters=20, prec="bf16")
-    torch.cuda.synchronize()
-    free1, _ = torch.cuda.mem_get_info()
+    gc.disable()
+    try:
+        free0, _ = torch.cuda.mem_get_info()
+        alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+        for _ in range(3):
+            pkg.polar_noalloc(a, 0.3, out=out, status=status, iters=20, prec="bf16")
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+    finally:
+        gc.enable()
     assert int(status.item()) == 0
     assert free1 == free0, (free0, free1)
     assert torch.cuda.memory_allocated() == alloc0
