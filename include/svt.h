@@ -67,11 +67,12 @@ typedef enum {
                      (hi*hi + hi*lo + lo*hi) with FP32 accumulation */
     SVT_BF16 = 2, /* polynomial steps in BF16 (FP32 accumulation); Gram, polish
                      and combine FP32-class; norms and the tau^2 shift in FP64 */
-    SVT_FP8_EXPERIMENTAL = 3 /* reserved, not built: every entry point returns
-                     SVT_ERR_UNSUPPORTED. Block-scaled e4m3 operands in even the
-                     first two polynomial steps put the relative error near 20 %,
-                     ten times the BF16 tier's 2e-2: later steps converge to the
-                     polar factor of the rounded iterate, they do not undo it */
+    SVT_FP8_EXPERIMENTAL = 3 /* no FP8 tier: every entry point but svt_polar_fp8 and
+                     svt_workspace_bytes_fp8 returns SVT_ERR_UNSUPPORTED for it. Those two
+                     take it as the BF16 tier plus an e4m3 step policy; measured, no policy
+                     is both faster and within the BF16 tier's 2e-2: an e4m3 rounding of
+                     an early iterate moves the matrix whose polar factor the later steps
+                     converge to, they do not undo it */
 } svt_precision;
 
 typedef enum {
@@ -408,6 +409,53 @@ svt_status svt_debug_gemm_bf16_ex(svt_ctx_t ctx, int nseg, const void *L_hi, con
                                   const void *R_hi, const void *R_lo, int64_t M, int64_t N,
                                   int64_t K, int64_t ldl, int64_t ldr, float *D, int64_t ldd,
                                   int sym, int tile, void *stream);
+
+/*
+ * FP8 experiment (the lower precision Section 3 weighs for speed): a BF16-tier solve
+ * with chosen polynomial steps on e4m3 operands (tcgen05.mma kind::f8f6f4, FP32
+ * accumulation). The products that write the operands also write e4m3 copies of them,
+ * scaled by powers of two fixed from the iterates' bounds (|entries| <= 1.03 -> x 256,
+ * saturated at 448); the BF16 results stay for everything else.
+ */
+typedef struct {
+    uint64_t p_steps;  /* bit t: the P chain's Z = a I + b Y + c Y^2 of step t takes Y^2 from
+                          an e4m3 copy of Y = X^T X (quintic steps) */
+    uint64_t s_steps;  /* bit t: S-chain step t (t >= 1, a BF16 step: past the leading
+                          FP32-class steps; other bits are ignored) runs Y = S^2, Y^2 and
+                          S Z on e4m3 operands */
+    int s_y2_only;     /* 1: in those S steps only the Y^2 product */
+    int reserved;      /* 0 */
+} svt_fp8_policy;
+
+/* Workspace svt_polar_fp8 needs: svt_workspace_bytes_ex of the BF16 tier plus one
+ * e4m3 k x k copy (k = min(m, n), rows padded) for p_steps != 0 and four for
+ * s_steps != 0. Errors: SVT_ERR_INVALID (null out or policy, non-zero reserved, a
+ * tier other than SVT_BF16 / SVT_FP8_EXPERIMENTAL), as svt_workspace_bytes_ex. */
+svt_status svt_workspace_bytes_fp8(int64_t m, int64_t n, const svt_options *opt,
+                                   const svt_fp8_policy *policy, size_t *out);
+
+/* svt_polar_ex with the FP8 policy: opt->prec must be SVT_BF16 or SVT_FP8_EXPERIMENTAL
+ * (both: the BF16 tier plus the policy); opt may be NULL (defaults). Same contract
+ * otherwise, with the workspace of svt_workspace_bytes_fp8. Errors: as svt_polar_ex;
+ * SVT_ERR_INVALID for a null policy, a non-zero reserved field or another tier.
+ *
+ * Measured on a GB300 (4096^2 inputs, 20 steps): e4m3 in the early steps of either
+ * chain leaves the result outside the BF16 tier's 2e-2 (0.24-1.1 in the P chain; the
+ * S chain diverges or reaches 4-5 %); Y^2 alone in the last five steps of either chain
+ * stays within it (1.01e-2 and 1.07e-2 against 1.00e-2 BF16 on a gapped spectrum) and
+ * is about 8 % slower: the products it speeds up are few and the e4m3 copies are extra
+ * stores. No policy is faster at the BF16 tier's accuracy. */
+svt_status svt_polar_fp8(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int64_t lda,
+                         float tau, const svt_options *opt, const svt_fp8_policy *policy, float *Y,
+                         int64_t ldy, svt_status *d_status, void *stream);
+
+/* Diagnostic for the e4m3 product path (used by the tests): D = L R^T with L M x K and
+ * R N x K e4m3 bytes, row-major (ldl, ldr in elements, multiples of 16; device pointers
+ * 16-byte aligned), FP32 accumulation, D FP32 row-major (ldd >= N); tile as
+ * svt_debug_gemm_bf16_ex. Errors: SVT_ERR_INVALID, SVT_ERR_CUDA. */
+svt_status svt_debug_gemm_e4m3(svt_ctx_t ctx, const void *L, const void *R, int64_t M, int64_t N,
+                               int64_t K, int64_t ldl, int64_t ldr, float *D, int64_t ldd, int tile,
+                               void *stream);
 
 /* Failure-path check of the device-side bounded waits: launches the product kernel
  * (fused form) on a one-tile table whose tile waits for its own completion, so the

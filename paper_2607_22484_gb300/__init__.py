@@ -9,4 +9,5 @@ is its Python binding.
 """
 from .binding import (BF16, FP32, FP64, Context, Matrix, Options, SVTError,  # noqa: F401
                       EXPORTS, lib, make_options, polar_noalloc, read_completion_stats,
-                      schedule_coeffs, status_str, workspace_bytes)
+                      fp8_policy, schedule_coeffs, status_str, workspace_bytes,
+                      workspace_bytes_fp8)

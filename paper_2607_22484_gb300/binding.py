@@ -45,6 +45,7 @@ EXPORTS = [
     "svt_prox_grad_step", "svt_complete", "svt_autotune_schedule", "svt_autotune_batch",
     "svt_ctx_profile_read_ex", "svt_debug_wait_timeout", "svt_polar_f64", "svt_serve_cancel",
     "svt_serve_metrics", "svt_ctx_debug", "svt_tuning_export", "svt_tuning_import",
+    "svt_polar_fp8", "svt_workspace_bytes_fp8", "svt_debug_gemm_e4m3",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -54,6 +55,11 @@ class Options(ctypes.Structure):
                 ("norm", ctypes.c_int), ("ell0", ctypes.c_double), ("delta", ctypes.c_double),
                 ("polish", ctypes.c_int), ("mode", ctypes.c_int), ("fuse", ctypes.c_int),
                 ("hp_steps", ctypes.c_int), ("tile", ctypes.c_int)]
+
+
+class Fp8Policy(ctypes.Structure):
+    _fields_ = [("p_steps", ctypes.c_uint64), ("s_steps", ctypes.c_uint64),
+                ("s_y2_only", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class Matrix(ctypes.Structure):
@@ -129,6 +135,11 @@ def lib():
         L.svt_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
         L.svt_serve_release.argtypes = [vp, ctypes.c_uint64]
         L.svt_serve_cancel.argtypes = [vp, ctypes.c_uint64]
+        L.svt_polar_fp8.argtypes = [vp, vp, i64, i64, i64, ctypes.c_float, ctypes.POINTER(Options),
+                                    ctypes.POINTER(Fp8Policy), vp, i64, vp, vp]
+        L.svt_workspace_bytes_fp8.argtypes = [i64, i64, ctypes.POINTER(Options),
+                                              ctypes.POINTER(Fp8Policy), ctypes.POINTER(ctypes.c_size_t)]
+        L.svt_debug_gemm_e4m3.argtypes = [vp, vp, vp, i64, i64, i64, i64, i64, vp, i64, i32, vp]
         L.svt_serve_metrics.argtypes = [vp, ctypes.c_char_p]
         L.svt_ctx_debug.argtypes = [vp, i32, i64]
         L.svt_tuning_export.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t,
@@ -210,6 +221,27 @@ def workspace_bytes(m: int, n: int, **opts) -> int:
     o = make_options(**opts)
     _check(lib().svt_workspace_bytes_ex(int(m), int(n), ctypes.byref(o), ctypes.byref(out)),
            "svt_workspace_bytes_ex")
+    return int(out.value)
+
+
+def fp8_policy(p_steps=(), s_steps=(), s_y2_only=False) -> Fp8Policy:
+    """svt_fp8_policy from step lists (bit t of p_steps / s_steps: step t on e4m3)."""
+    def bits(steps):
+        v = 0
+        for t in steps:
+            if not 0 <= int(t) < 64:
+                raise ValueError("FP8 policy steps are 0..63")
+            v |= 1 << int(t)
+        return v
+    return Fp8Policy(bits(p_steps), bits(s_steps), 1 if s_y2_only else 0, 0)
+
+
+def workspace_bytes_fp8(m: int, n: int, p_steps=(), s_steps=(), s_y2_only=False, **opts) -> int:
+    out = ctypes.c_size_t(0)
+    o = make_options(**dict({"prec": "bf16"}, **opts))
+    pol = fp8_policy(p_steps, s_steps, s_y2_only)
+    _check(lib().svt_workspace_bytes_fp8(int(m), int(n), ctypes.byref(o), ctypes.byref(pol),
+                                         ctypes.byref(out)), "svt_workspace_bytes_fp8")
     return int(out.value)
 
 
@@ -384,6 +416,39 @@ class Context:
                                    ctypes.c_void_p(st_ptr), ctypes.c_void_p(_stream_ptr(stream))),
                "svt_polar_f64")
         return out
+
+    def polar_fp8(self, A, tau: float, p_steps=(), s_steps=(), s_y2_only=False, out=None,
+                  status=None, stream=None, **opts):
+        """svt_polar_fp8: the BF16 tier with the listed steps on e4m3 operands (p_steps:
+        the P chain's Y^2 products; s_steps: S-chain steps, all products or Y^2 only)."""
+        import torch
+        a_ptr, m, n, lda = _f32_matrix(A, "A")
+        if out is None:
+            out = torch.empty((m, n), dtype=torch.float32, device=A.device)
+        y_ptr, ym, yn, ldy = _f32_matrix(out, "out")
+        if (ym, yn) != (m, n):
+            raise ValueError("out has the wrong shape")
+        pol = fp8_policy(p_steps, s_steps, s_y2_only)
+        o = make_options(**dict({"prec": "bf16"}, **opts))
+        self.ensure_workspace(workspace_bytes_fp8(m, n, p_steps, s_steps, s_y2_only, **opts))
+        st_ptr = status.data_ptr() if status is not None else None
+        _check(lib().svt_polar_fp8(self.handle, ctypes.c_void_p(a_ptr), m, n, lda,
+                                   ctypes.c_float(tau), ctypes.byref(o), ctypes.byref(pol),
+                                   ctypes.c_void_p(y_ptr), ldy, ctypes.c_void_p(st_ptr),
+                                   ctypes.c_void_p(_stream_ptr(stream))), "svt_polar_fp8")
+        return out
+
+    def debug_gemm_e4m3(self, L, R, D, K=None, tile=0, stream=None):
+        """D = L R^T over the first K columns (default: all) of the e4m3 byte tensors
+        L (M rows) and R (N rows) (svt_debug_gemm_e4m3)."""
+        M, N = L.shape[0], R.shape[0]
+        K = L.shape[1] if K is None else int(K)
+        _check(lib().svt_debug_gemm_e4m3(self.handle, ctypes.c_void_p(L.data_ptr()),
+                                         ctypes.c_void_p(R.data_ptr()), M, N, K, L.stride(0),
+                                         R.stride(0), ctypes.c_void_p(D.data_ptr()), D.stride(0),
+                                         int(tile), ctypes.c_void_p(_stream_ptr(stream))),
+               "svt_debug_gemm_e4m3")
+        return D
 
     def prox_grad_step(self, X, M, mask, lam: float, Z=None, step: float = 1.0, status=None,
                        stream=None, **opts):

@@ -35,6 +35,7 @@ struct DepProduct {
     int tiles_m, tiles_n;   // tile grid
     int valid;              // CTA tiles with work (the completion-count unit)
     const double *theta_src, *norm_acc;  // norm read by the scales / accumulated
+    const void *f = nullptr;  // written: an extra copy in the output's orientation (e4m3)
 };
 
 // What one product waits for (the fields of the same names in TcProblem).
@@ -119,7 +120,7 @@ inline bool derive_fused_deps(const std::vector<DepProduct> &ps, bool strips, in
                 before_store(it->second);
         }
         // WAR / WAW on the buffers this product writes
-        const void *outs[2] = {p.o, p.t};
+        const void *outs[3] = {p.o, p.t, p.f};
         for (const void *b : outs) {
             if (!b)
                 continue;
@@ -146,6 +147,10 @@ inline bool derive_fused_deps(const std::vector<DepProduct> &ps, bool strips, in
         if (p.t) {
             writers[p.t] = {pid, 2};
             readers[p.t].clear();
+        }
+        if (p.f) {
+            writers[p.f] = {pid, p.sym ? 3 : 1};
+            readers[p.f].clear();
         }
         if (p.norm_acc)
             norm_writer[p.norm_acc] = pid;

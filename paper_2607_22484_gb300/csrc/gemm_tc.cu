@@ -32,6 +32,7 @@
 #include <cstddef>
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -317,6 +318,41 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
+// Instruction descriptor of kind::f8f6f4: e4m3 x e4m3 -> FP32 (A and B format code 0),
+// both operands K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int m, int n)
+{
+    return (1u << 4)                       // D format FP32
+           | ((uint32_t)(n >> 3) << 17)    // N / 8
+           | ((uint32_t)(m >> 4) << 24);   // M / 16
+}
+
+// A compile-time bool passed as a value (selects a loop body's instruction kind).
+template <bool B>
+struct BoolTag {
+    static constexpr bool value = B;
+};
+
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_e4m3_pair(uint32_t d_tmem, uint64_t a, uint64_t b,
+                                              uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile(
@@ -539,6 +575,9 @@ struct EpiHot {
     int64_t ldc, ldo, ldt;
     float alpha, beta, gamma;
     int M, N, sym, otma, ttma, c_kind, c_trans, o_kind, o_trans, t_kind;
+    void *f0;          // e4m3 copy (FP8 experiment), null: none
+    int64_t ldf;
+    float fscale;
     int strip_base, tiles_m;  // fused solves: the problem's strip counters
 };
 
@@ -645,6 +684,55 @@ __device__ __forceinline__ void c_apply(const EpiHot &h, const CRaw &cr, bool ve
 // Fallback staging: 32 x 32 floats, element (a, b) at a * 32 + (b ^ a); rows and
 // columns are both free of bank conflicts.
 __device__ __forceinline__ int xs_idx(int a, int b) { return a * 32 + (b ^ a); }
+
+// e4m3 bytes of scale * v, saturated (the FP8 experiment's operand copies), in the
+// layout store_block uses: 16 rows x 32 bytes per instruction. Kept out of line so
+// that the BF16 epilogue's code is what it is without it.
+__device__ __noinline__ void store_block_e4m3(const float *st, void *p0, int64_t ld, int64_t r0,
+                                              int64_t c0, int64_t M, int64_t N, bool trans,
+                                              bool symdiag, int lane, float scale)
+{
+    const int64_t orow0 = trans ? c0 : r0, ocol0 = trans ? r0 : c0;
+    const int64_t orows = trans ? N : M, ocols = trans ? M : N;
+    // e4m3 bytes of scale * v, saturated: 16 rows x 32 bytes per instruction
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int a = k * 16 + (lane >> 1);
+        const int q = lane & 1;  // columns 16 q .. 16 q + 15
+        const int64_t R = orow0 + a;
+        float x[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int b = q * 16 + j;
+            int sa, sb;
+            if (trans) { sa = b; sb = a; }
+            else if (symdiag && a > b) { sa = b; sb = a; }
+            else { sa = a; sb = b; }
+            x[j] = scale * st[xs_idx(sa, sb)];
+        }
+        if (R >= orows)
+            continue;
+        const int64_t C = ocol0 + q * 16;
+        uint8_t *p = static_cast<uint8_t *>(p0) + R * ld + C;
+        if (C + 16 <= ocols && aligned16(p)) {
+            uint32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(x[4 * j], x[4 * j + 1]),
+                                                             __NV_SATFINITE, __NV_E4M3);
+                const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(x[4 * j + 2], x[4 * j + 3]),
+                                                             __NV_SATFINITE, __NV_E4M3);
+                w[j] = lo | (hi << 16);
+            }
+            *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (C + j < ocols)
+                    p[j] = __nv_cvt_float_to_fp8(x[j], __NV_SATFINITE, __NV_E4M3);
+        }
+    }
+}
 
 // Store a 32 x 32 block held in shared memory `st` (st[a][b] = value of tile
 // element (r0 + a, c0 + b)) to global memory, coalesced: warp lanes cover whole
@@ -879,7 +967,7 @@ __device__ __forceinline__ void epilogue_finish(const EpiHot &h, int64_t r0, int
         tma_store_block<NSTG>(v, h.t_kind, true, &h.maps[2], &h.maps[3], (int)r0, (int)c0, stg,
                               slot, lane);
     const bool need_plain = (h.o_kind != O_NONE && !o_tma) || (h.sym && !diag_block && !h.otma) ||
-                            (h.t_kind != O_NONE && !h.ttma);
+                            (h.t_kind != O_NONE && !h.ttma) || h.f0 != nullptr;
     if (!need_plain)
         return;
     // Coalesced plain-store path: stage with a swizzled pitch, then whole row segments.
@@ -897,6 +985,11 @@ __device__ __forceinline__ void epilogue_finish(const EpiHot &h, int64_t r0, int
         store_block(st, h.o_kind, h.o0, h.o1, h.ldo, r0, c0, h.M, h.N, true, false, lane);
     if (h.t_kind != O_NONE && !h.ttma)
         store_block(st, h.t_kind, h.t0, h.t1, h.ldt, r0, c0, h.M, h.N, true, false, lane);
+    if (h.f0) {  // the e4m3 copy, mirrored like the output for symmetric products
+        store_block_e4m3(st, h.f0, h.ldf, r0, c0, h.M, h.N, false, symdiag, lane, h.fscale);
+        if (h.sym && !diag_block)
+            store_block_e4m3(st, h.f0, h.ldf, r0, c0, h.M, h.N, true, false, lane, h.fscale);
+    }
     __syncwarp();
 }
 
@@ -930,6 +1023,9 @@ __device__ __forceinline__ void load_hot(EpiHot &h, const TcProblem &P, const Ca
     h.o_kind = e.o_kind;
     h.o_trans = e.o_trans;
     h.t_kind = e.t_kind;
+    h.f0 = e.f0;
+    h.ldf = e.ldf;
+    h.fscale = e.fscale;
     double alpha = e.alpha;
     if (P.patch) {  // grouped / fused launch: per-call fields
         const CallRec &cr = calls[P.call_idx];
@@ -1095,7 +1191,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             if (!tc.valid)
                 continue;
             const TcProblem &P = prob_at(L, tc.prob);
-            const int kblocks = (P.K + kBK - 1) / kBK;
+            // A k-block is one 128-byte swizzle row: 64 BF16 or 128 e4m3 elements.
+            const int kshift = P.fp8 ? 7 : 6;
+            const int kblocks = (P.K + (1 << kshift) - 1) >> kshift;
             const int row0 = (PAIR ? 2 * tc.tm + (int)rank : tc.tm) * kBM;
             const int col0 = tc.tn * BN + (int)rank * B_ROWS;
             if (CHAIN) {
@@ -1141,12 +1239,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                         const uint32_t fb = peer_addr(&full[stage], 0);
                         if (leader)
                             mbar_expect_tx(&full[stage], 2u * (uint32_t)(A_BYTES + B_BYTES));
-                        tma_load_2d_pair(sA + stage * A_BYTES, mL, kb * kBK, row0, fb);
-                        tma_load_2d_pair(sB + stage * B_BYTES, mR, kb * kBK, col0, fb);
+                        tma_load_2d_pair(sA + stage * A_BYTES, mL, kb << kshift, row0, fb);
+                        tma_load_2d_pair(sB + stage * B_BYTES, mR, kb << kshift, col0, fb);
                     } else {
                         mbar_expect_tx(&full[stage], (uint32_t)(A_BYTES + B_BYTES));
-                        tma_load_2d(sA + stage * A_BYTES, mL, kb * kBK, row0, &full[stage]);
-                        tma_load_2d(sB + stage * B_BYTES, mR, kb * kBK, col0, &full[stage]);
+                        tma_load_2d(sA + stage * A_BYTES, mL, kb << kshift, row0, &full[stage]);
+                        tma_load_2d(sB + stage * B_BYTES, mR, kb << kshift, col0, &full[stage]);
                     }
                     issued |= 1u << stage;
                     issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
@@ -1170,7 +1268,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             }
     } else if (warp == 1 && lane == 0 && (!PAIR || leader)) {
         // ------------------------------------------------ MMA issuer
-        constexpr uint32_t idesc = idesc_bf16(TILE_ROWS, BN);
         int stage = 0;
         uint32_t phase = 0;
         int buf = 0;
@@ -1204,41 +1301,55 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             if (!tc.valid)
                 continue;
             const TcProblem &P = prob_at(L, tc.prob);
-            const int kblocks = (P.K + kBK - 1) / kBK;
             if (!wait_bar<PAIR>(&tempty[buf], tphase ^ 1u, abort_flag, status0, kWaitTimeoutNs))
                 break;
             tc_fence_after();
             const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
-            uint32_t acc = 0;
-            for (int sg = 0; sg < P.nseg && ok; ++sg) {
-                for (int kb = 0; kb < kblocks; ++kb) {
-                    if (!mbar_wait(&full[stage], phase, abort_flag, status0, kWaitTimeoutNs)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t a0 = smem_u32(sA + stage * A_BYTES);
-                    const uint32_t b0 = smem_u32(sB + stage * B_BYTES);
+            // The tile's k-loop, one copy per operand kind chosen once per tile, so that
+            // the BF16 loop carries no test of the kind: for each segment and k-block,
+            // wait for the stage's copies, issue four MMAs over its 128 bytes of each row
+            // (K = 16 BF16 or 32 e4m3 elements each) and release the stage.
+            auto k_loop = [&](auto f8_tag) -> bool {
+                constexpr bool F8 = decltype(f8_tag)::value;
+                constexpr uint32_t id = F8 ? idesc_e4m3(TILE_ROWS, BN) : idesc_bf16(TILE_ROWS, BN);
+                const int kblocks = F8 ? (P.K + 2 * kBK - 1) / (2 * kBK) : (P.K + kBK - 1) / kBK;
+                uint32_t acc = 0;
+                for (int sg = 0; sg < P.nseg; ++sg) {
+                    for (int kb = 0; kb < kblocks; ++kb) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag, status0, kWaitTimeoutNs))
+                            return false;
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(sA + stage * A_BYTES);
+                        const uint32_t b0 = smem_u32(sB + stage * B_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        for (int kk = 0; kk < kBK / 16; ++kk) {
+                            const uint64_t ad = sw128_desc(a0 + kk * 32), bd = sw128_desc(b0 + kk * 32);
+                            if (F8) {
+                                if (PAIR)
+                                    mma_e4m3_pair(d_tmem, ad, bd, id, acc);
+                                else
+                                    mma_e4m3(d_tmem, ad, bd, id, acc);
+                            } else {
+                                if (PAIR)
+                                    mma_bf16_pair(d_tmem, ad, bd, id, acc);
+                                else
+                                    mma_bf16(d_tmem, ad, bd, id, acc);
+                            }
+                            acc = 1;
+                        }
                         if (PAIR)
-                            mma_bf16_pair(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32),
-                                          idesc, acc);
+                            mma_commit_both(&empty[stage]);
                         else
-                            mma_bf16(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32),
-                                     idesc, acc);
-                        acc = 1;
-                    }
-                    if (PAIR)
-                        mma_commit_both(&empty[stage]);
-                    else
-                        mma_commit(&empty[stage]);
-                    if (++stage == STAGES) {
-                        stage = 0;
-                        phase ^= 1u;
+                            mma_commit(&empty[stage]);
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
                     }
                 }
-            }
+                return true;
+            };
+            ok = P.fp8 ? k_loop(BoolTag<true>{}) : k_loop(BoolTag<false>{});
             if (!ok)
                 break;
             if (PAIR)

@@ -48,6 +48,11 @@ struct Resolved {
     int fuse;       // one persistent launch for all products of a solve
     int tile;       // requested tile-width code (0 automatic); read by svt_polar_ex only
     int out64 = 0;  // FP64 tier only: the result is stored as FP64 (svt_polar_f64)
+    // FP8 experiment (BF16 tier only): bit t of fp8_p -- the P chain's Y^2 product of
+    // step t on e4m3 copies of Y; bit t of fp8_s -- the S chain's step t (a BF16 step)
+    // on e4m3 operands, all three products, or only Y^2 when fp8_s_y2.
+    uint64_t fp8_p = 0, fp8_s = 0;
+    int fp8_s_y2 = 0;
 };
 
 bool resolve(const svt_options *in, Resolved *r);
@@ -71,6 +76,7 @@ struct Layout {
     int max_problems = 0;    // capacity of the fused counters / table
     size_t fused_tab = 0, fused_tab_bytes = 0;
     Buf X[2], Xt[2], XtLo0, S[2], Yp, Zp, Ys, Zs, ZPp, ZSp, B, Sp;
+    Buf Yp8, S8[2], Ys8, Zs8;  // e4m3 copies (FP8 experiment), 1-byte elements
     size_t total = 0;
 };
 
@@ -117,6 +123,7 @@ struct Plan {
         const void *l, *r, *c, *o, *t;
         int o_trans;
         const double *theta_src, *norm_acc;
+        const void *f;  // the e4m3 copy written (FP8 experiment), null: none
     };
     std::vector<ProbIO> tc_io;
     bool uses_strips = false;       // the fused launch waits on strip counters
@@ -169,12 +176,15 @@ struct Key {
     int force_bn;
     int fuse;
     int out64;
+    uint64_t fp8_p, fp8_s;
+    int fp8_s_y2;
     bool operator<(const Key &o) const
     {
         return std::tie(m, n, iters, prec, schedule, norm, polish, mode, hp_steps, ell0, delta,
-                        ws_base, force_bn, fuse, out64) <
+                        ws_base, force_bn, fuse, out64, fp8_p, fp8_s, fp8_s_y2) <
                std::tie(o.m, o.n, o.iters, o.prec, o.schedule, o.norm, o.polish, o.mode,
-                        o.hp_steps, o.ell0, o.delta, o.ws_base, o.force_bn, o.fuse, o.out64);
+                        o.hp_steps, o.ell0, o.delta, o.ws_base, o.force_bn, o.fuse, o.out64,
+                        o.fp8_p, o.fp8_s, o.fp8_s_y2);
     }
 };
 

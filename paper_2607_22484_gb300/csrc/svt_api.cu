@@ -76,6 +76,24 @@ bool encode_bf16_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t co
     return r == CUDA_SUCCESS;
 }
 
+bool encode_e4m3_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld,
+                     int box_rows)
+{
+    std::call_once(g_encode_once, resolve_encode);
+    if (!g_encode || !ptr || rows <= 0 || cols <= 0 || (ld % 16) != 0 ||
+        (reinterpret_cast<uintptr_t>(ptr) & 15) != 0)
+        return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * kBK), (cuuint32_t)box_rows};  // one 128-byte row
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(ptr), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 bool encode_store_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld,
                       bool f32)
 {
@@ -168,6 +186,8 @@ bool resolve(const svt_options *in, Resolved *r)
         return false;
     r->tile = (o.prec == SVT_FP64) ? 0 : o.tile;
     r->out64 = 0;
+    r->fp8_p = r->fp8_s = 0;
+    r->fp8_s_y2 = 0;
     return true;
 }
 
@@ -239,6 +259,14 @@ Layout make_layout(int64_t m, int64_t n, const Resolved &r)
     L.ZSp = make_buf(a, L.N, L.N, L.esz, !f64);
     L.B = make_buf(a, L.M, L.N, L.esz, !f64);
     L.Sp = make_buf(a, L.N, L.N, L.esz, !f64);
+    if (r.fp8_p && !skipP)
+        L.Yp8 = make_buf(a, L.N, L.N, 1, false);
+    if (r.fp8_s) {
+        for (int i = 0; i < 2; ++i)
+            L.S8[i] = make_buf(a, L.N, L.N, 1, false);
+        L.Ys8 = make_buf(a, L.N, L.N, 1, false);
+        L.Zs8 = make_buf(a, L.N, L.N, 1, false);
+    }
     if (!f64 && r.fuse) {
         L.fused_tab_bytes = align_up(sizeof(TcProblem) * (size_t)L.max_problems, kAlign) +
                             align_up(sizeof(int) * (size_t)(L.max_problems + 1), kAlign);
@@ -296,6 +324,13 @@ struct Builder {
         e.t1 = pair ? ptr(b.lo) : nullptr;
         e.ldt = b.ld;
     }
+    // The e4m3 copy of a product's result (FP8 experiment), scaled by `scale`.
+    void set_f(Epi &e, const Buf &b, float scale)
+    {
+        e.f0 = ptr(b.hi);
+        e.ldf = b.ld;
+        e.fscale = scale;
+    }
     void set_c(Epi &e, const Buf &b, double beta)
     {
         const bool f64 = plan->opt.prec == SVT_FP64;
@@ -309,9 +344,26 @@ struct Builder {
     // One product D = L R^T over the segment pattern implied by the operands'
     // hi/lo parts (1, 2 or 3 BF16 products).
     bool tc_problem(TcProblem &p, const Buf &L, const Buf &R, int M, int N, int K, bool sym,
-                    const Epi &e, int bn)
+                    const Epi &e, int bn, bool fp8 = false)
     {
         std::memset(&p, 0, sizeof(p));
+        if (fp8) {  // e4m3 operands (FP8 experiment): one segment, hi buffers only
+            if (!encode_e4m3_map(&p.mapL[0], ptr(L.hi), L.rows, L.cols, L.ld, kBM) ||
+                !encode_e4m3_map(&p.mapR[0], ptr(R.hi), R.rows, R.cols, R.ld, r_box_rows(bn)))
+                return false;
+            p.fp8 = 1;
+            p.nseg = 1;
+            p.M = M;
+            p.N = N;
+            p.K = K;
+            p.sym = sym ? 1 : 0;
+            p.strip_base = -1;
+            p.tiles_m = (M + tile_rows(bn) - 1) / tile_rows(bn);
+            p.tiles_n = (N + tile_cols(bn) - 1) / tile_cols(bn);
+            p.ep = e;
+            attach_store_maps(p);
+            return true;
+        }
         if (!encode_bf16_map(&p.mapL[0], ptr(L.hi), L.rows, L.cols, L.ld, kBM))
             return false;
         if (!encode_bf16_map(&p.mapR[0], ptr(R.hi), R.rows, R.cols, R.ld, r_box_rows(bn)))
@@ -360,6 +412,7 @@ struct Builder {
         Epi e;
         int patch;
         int chain = 0;  // 0 P chain, 1 S chain, 2 both (combine)
+        bool fp8 = false;  // e4m3 operands (FP8 experiment)
     };
 
     bool emit(const std::vector<Prod> &prods)
@@ -395,13 +448,13 @@ struct Builder {
         int start = 0;
         for (size_t i = 0; i < prods.size(); ++i) {
             const Prod &q = prods[i];
-            if (!tc_problem(l.p[i], *q.L, *q.R, q.M, q.N, q.K, q.sym, q.e, bn))
+            if (!tc_problem(l.p[i], *q.L, *q.R, q.M, q.N, q.K, q.sym, q.e, bn, q.fp8))
                 return false;
             plan->tc_chain.push_back(q.chain);
             plan->tc_io.push_back({ptr(q.L->hi), ptr(q.R->hi),
                                    (q.patch & PT_C_IS_A) ? nullptr : q.e.c0,
                                    (q.patch & PT_O_IS_Y) ? nullptr : q.e.o0, q.e.t0,
-                                   q.e.o_trans, q.e.theta_src, q.e.norm_acc});
+                                   q.e.o_trans, q.e.theta_src, q.e.norm_acc, q.e.f0});
             l.tile_start[i] = start;
             start += tc_num_tiles(l.p[i], bn);
             if (q.patch)
@@ -415,7 +468,8 @@ struct Builder {
             fl += (q.sym ? 1.0 : 2.0) * (double)q.M * (double)q.N * (double)q.K;
         for (int i = 0; i < l.nprob; ++i) {
             const TcProblem &tp = l.p[i];
-            const double kpad = (double)((tp.K + kBK - 1) / kBK * kBK);
+            const int kb = tp.fp8 ? 2 * kBK : kBK;
+            const double kpad = (double)((tp.K + kb - 1) / kb * kb);
             // each CTA tile: 128 rows x tile_cols(bn) columns over the padded K
             tfl += (double)tp.nseg * (double)tc_valid_ctas(tp, bn) * 2.0 * kBM *
                    (double)tile_cols(bn) * kpad;
@@ -488,6 +542,23 @@ struct Builder {
                 return false;
         }
 
+        // FP8 experiment: S-chain step t runs all three products on e4m3 copies (a BF16
+        // quintic step after the first); the copies it reads are written by the products
+        // that produce S, Y and Z. Scales are powers of two from the iterates' bounds:
+        // the normalised iterates and their squares stay below ~1.03 (x 256 < 448, the
+        // largest e4m3), the P chain's first Y = X0^T X0 below ||X0||_F^2 < 2 (x 128), and
+        // Z = a + b y + c y^2 below its maximum over y in [0, 1.1].
+        auto f8s_all_at = [&](int t) {
+            return t >= 1 && t < o.iters && o.schedule == SVT_SCHED_PE5 && !s_pair(t) &&
+                   ((o.fp8_s >> t) & 1ull) && !o.fp8_s_y2;
+        };
+        auto e4m3_scale = [](double bound) {
+            double sc = 1.0;
+            while (sc * 2.0 * bound <= 448.0 && sc < 32768.0)
+                sc *= 2.0;
+            return (float)sc;
+        };
+        const float s_it = 256.f;
         // Chains.
         int cur = 0;
         for (int t = 0; t < o.iters; ++t) {
@@ -497,6 +568,17 @@ struct Builder {
             const int nxt = 1 - cur;
             const bool hp = s_pair(t);  // this S step in the FP32-class tier
             const Buf Sc = view(L.S[cur], hp), Ysv = view(L.Ys, hp), Zsv = view(L.Zs, hp);
+            const bool f8p = quintic && !skipP && ((o.fp8_p >> t) & 1ull);
+            const bool f8s = quintic && !hp && t >= 1 && ((o.fp8_s >> t) & 1ull);
+            const bool f8s_all = f8s_all_at(t), f8s_next = f8s_all_at(t + 1);
+            const float s_yp = first ? 128.f : 256.f;
+            double zmax = std::max(std::fabs(a), std::fabs(a + 1.1 * b + 1.21 * c));
+            if (c != 0.0) {
+                const double yv = -b / (2.0 * c);
+                if (yv > 0.0 && yv < 1.1)
+                    zmax = std::max(zmax, std::fabs(a + b * yv + c * yv * yv));
+            }
+            const float s_z = e4m3_scale(zmax);
             // theta sources for the first step
             const double *thP = nullptr, *thS = nullptr;
             double powP = 0.5, powS = 0.5;
@@ -527,6 +609,8 @@ struct Builder {
                     set_out(e, L.Yp, pairs);
                     if (first && o.norm == SVT_NORM_GRAM)
                         e.norm_acc = scal(SC_NRM_YP);
+                    if (f8p)
+                        set_f(e, L.Yp8, s_yp);
                     s1.push_back({&L.Xt[cur], &L.Xt[cur], N, N, M, true, e, 0});
                 }
                 {
@@ -534,7 +618,14 @@ struct Builder {
                     set_out(e, L.Ys, hp);
                     if (first && o.norm == SVT_NORM_GRAM)
                         e.norm_acc = scal(SC_NRM_YS);
-                    s1.push_back({&Sc, &Sc, N, N, N, true, e, 0, 1});
+                    if (f8s)
+                        set_f(e, L.Ys8, s_it);
+                    if (f8s_all) {
+                        e.alpha = 1.0 / ((double)s_it * s_it);
+                        s1.push_back({&L.S8[cur], &L.S8[cur], N, N, N, true, e, 0, 1, true});
+                    } else {
+                        s1.push_back({&Sc, &Sc, N, N, N, true, e, 0, 1});
+                    }
                 }
                 if (!emit(s1))
                     return false;
@@ -547,7 +638,12 @@ struct Builder {
                     set_c(e, L.Yp, b);
                     set_out(e, L.Zp, pairs);
                     theta(e, thP, powP, 5, 3, 1);
-                    s2.push_back({&L.Yp, &L.Yp, N, N, N, true, e, 0});
+                    if (f8p) {  // Y^2 from the e4m3 copy of Y: undo its scale squared
+                        e.alpha = c / ((double)s_yp * s_yp);
+                        s2.push_back({&L.Yp8, &L.Yp8, N, N, N, true, e, 0, 0, true});
+                    } else {
+                        s2.push_back({&L.Yp, &L.Yp, N, N, N, true, e, 0});
+                    }
                 }
                 {
                     Epi e = epi0();
@@ -556,7 +652,14 @@ struct Builder {
                     set_c(e, Ysv, b);
                     set_out(e, L.Zs, hp);
                     theta(e, thS, powS, 5, 3, 1);
-                    s2.push_back({&Ysv, &Ysv, N, N, N, true, e, 0, 1});
+                    if (f8s_all)
+                        set_f(e, L.Zs8, s_z);
+                    if (f8s) {
+                        e.alpha = c / ((double)s_it * s_it);
+                        s2.push_back({&L.Ys8, &L.Ys8, N, N, N, true, e, 0, 1, true});
+                    } else {
+                        s2.push_back({&Ysv, &Ysv, N, N, N, true, e, 0, 1});
+                    }
                 }
                 if (!emit(s2))
                     return false;
@@ -593,7 +696,14 @@ struct Builder {
             {
                 Epi e = epi0();
                 set_out(e, L.S[nxt], s_pair(t + 1));
-                s3.push_back({&Sc, &Zsv, N, N, N, true, e, 0, 1});
+                if (f8s_next)
+                    set_f(e, L.S8[nxt], s_it);
+                if (f8s_all) {
+                    e.alpha = 1.0 / ((double)s_it * s_z);
+                    s3.push_back({&L.S8[cur], &L.Zs8, N, N, N, true, e, 0, 1, true});
+                } else {
+                    s3.push_back({&Sc, &Zsv, N, N, N, true, e, 0, 1});
+                }
             }
             if (!emit(s3))
                 return false;
@@ -957,7 +1067,7 @@ svt_status build_fused(svt_ctx *ctx, Plan &P)
             if (tp.patch & PT_O_IS_Y)
                 tp.o_tma = 0;  // the caller's output: plain coalesced stores
             dps.push_back({io.l, io.r, io.c, io.o, io.t, io.o_trans, tp.sym, chain, tp.tiles_m,
-                           tp.tiles_n, tc_valid_ctas(tp, bn), io.theta_src, io.norm_acc});
+                           tp.tiles_n, tc_valid_ctas(tp, bn), io.theta_src, io.norm_acc, io.f});
             starts.push_back(total);
             total += tc_num_tiles(tp, bn);
             probs.push_back(tp);
@@ -1053,7 +1163,7 @@ svt_status get_plan(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r, size_
     if (force_bn == 0 && r.fuse && r.prec != SVT_FP64)
         force_bn = fused_auto_width(m, n);
     Key k{m, n, r.iters, r.prec, r.schedule, r.norm, r.polish, r.mode, r.hp_steps, r.ell0, r.delta,
-          ws_base, force_bn, r.fuse, r.out64};
+          ws_base, force_bn, r.fuse, r.out64, r.fp8_p, r.fp8_s, r.fp8_s_y2};
     auto it = ctx->plans.find(k);
     if (it != ctx->plans.end()) {
         *out = it->second.get();
@@ -1605,6 +1715,106 @@ svt_status svt_debug_gemm_bf16_ex(svt_ctx_t ctx, int nseg, const void *L_hi, con
     cudaError_t e = tc_gemm_launch(l, bn, ctx->num_sms, static_cast<cudaStream_t>(stream));
     ctx->launches += 1;
     return e == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;
+}
+
+svt_status svt_debug_gemm_e4m3(svt_ctx_t ctx, const void *L, const void *R, int64_t M, int64_t N,
+                               int64_t K, int64_t ldl, int64_t ldr, float *D, int64_t ldd, int tile,
+                               void *stream)
+{
+    if (!ctx || !L || !R || !D || M <= 0 || N <= 0 || K <= 0 || ldl < K || ldr < K || ldd < N ||
+        (ldl % 16) || (ldr % 16))
+        return SVT_ERR_INVALID;
+    if (tile != 0 && tile != 128 && tile != 256 && tile != kBnPair)
+        return SVT_ERR_INVALID;
+    if (M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2)
+        return SVT_ERR_UNSUPPORTED;
+    const int bn = tile ? tile : (N > 128 ? 256 : 128);
+    TcLaunch l;
+    std::memset(&l, 0, sizeof(l));
+    l.nprob = 1;
+    TcProblem &p = l.p[0];
+    if (!encode_e4m3_map(&p.mapL[0], L, M, K, ldl, kBM) ||
+        !encode_e4m3_map(&p.mapR[0], R, N, K, ldr, r_box_rows(bn)))
+        return SVT_ERR_INVALID;
+    p.fp8 = 1;
+    p.nseg = 1;
+    p.M = (int)M;
+    p.N = (int)N;
+    p.K = (int)K;
+    p.strip_base = -1;
+    p.tiles_m = (int)((M + tile_rows(bn) - 1) / tile_rows(bn));
+    p.tiles_n = (int)((N + tile_cols(bn) - 1) / tile_cols(bn));
+    p.ep.alpha = 1.0;
+    p.ep.o_kind = O_F32;
+    p.ep.o0 = D;
+    p.ep.ldo = ldd;
+    attach_store_maps(p);
+    l.tile_start[0] = 0;
+    l.tile_start[1] = tc_num_tiles(p, bn);
+    if (cudaSetDevice(ctx->device) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    cudaError_t e = tc_gemm_launch(l, bn, ctx->num_sms, static_cast<cudaStream_t>(stream));
+    ctx->launches += 1;
+    return e == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;
+}
+
+// The BF16 tier's resolved options with an FP8 policy's steps on e4m3 operands.
+static svt_status resolve_fp8(const svt_options *opt, const svt_fp8_policy *policy, Resolved *r)
+{
+    if (!policy || policy->reserved != 0)
+        return SVT_ERR_INVALID;
+    svt_options o;
+    if (opt)
+        o = *opt;
+    else
+        svt_options_default(&o);
+    if (o.prec == SVT_FP8_EXPERIMENTAL)
+        o.prec = SVT_BF16;
+    if (o.prec != SVT_BF16)
+        return SVT_ERR_INVALID;
+    if (svt_status st = resolve_status(&o, r))
+        return st;
+    r->fp8_p = policy->p_steps;
+    r->fp8_s = policy->s_steps;
+    r->fp8_s_y2 = policy->s_y2_only ? 1 : 0;
+    return SVT_OK;
+}
+
+svt_status svt_workspace_bytes_fp8(int64_t m, int64_t n, const svt_options *opt,
+                                   const svt_fp8_policy *policy, size_t *out)
+{
+    Resolved r;
+    if (!out || m <= 0 || n <= 0)
+        return SVT_ERR_INVALID;
+    if (svt_status st = resolve_fp8(opt, policy, &r))
+        return st;
+    *out = make_layout(m, n, r).total;
+    return SVT_OK;
+}
+
+svt_status svt_polar_fp8(svt_ctx_t ctx, const float *A, int64_t m, int64_t n, int64_t lda,
+                         float tau, const svt_options *opt, const svt_fp8_policy *policy, float *Y,
+                         int64_t ldy, svt_status *d_status, void *stream)
+{
+    if (!ctx)
+        return SVT_ERR_INVALID;
+    svt_status st = validate(A, m, n, lda, tau, Y, ldy);
+    if (st != SVT_OK)
+        return st;
+    Resolved r;
+    if ((st = resolve_fp8(opt, policy, &r)) != SVT_OK)
+        return st;
+    if (serve_busy(ctx))
+        return SVT_ERR_BUSY;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    Plan *plan = nullptr;
+    st = plan_for_solve(ctx, m, n, r, &plan);
+    if (st != SVT_OK)
+        return st;
+    CallArgs a{A, lda, tau, Y, ldy, d_status};
+    return run_plan(ctx, *plan, a, static_cast<cudaStream_t>(stream));
 }
 
 svt_status svt_debug_wait_timeout(svt_ctx_t ctx, svt_status *d_status, void *stream)

@@ -35,7 +35,7 @@ inline int r_box_rows(int bn) { return bn == kBnPair ? 128 : bn; }  // R rows on
 inline int ctas_per_tile(int bn) { return bn == kBnPair ? 2 : 1; }
 
 enum CKind : int { C_NONE = 0, C_BF16 = 1, C_PAIR = 2, C_F32 = 3, C_F64 = 4 };
-enum OKind : int { O_NONE = 0, O_BF16 = 1, O_PAIR = 2, O_F32 = 3, O_F64 = 4 };
+enum OKind : int { O_NONE = 0, O_BF16 = 1, O_PAIR = 2, O_F32 = 3, O_F64 = 4, O_E4M3 = 5 };
 
 // Device-side scalar slots of one solve (FP64, in the workspace).
 enum Scal : int {
@@ -69,6 +69,12 @@ struct Epi {
     const double *diag;              // v(r, r) = diag[r] * dss[0] - dss[1] (FP64)
     const double *dss;
     int *status;                     // device status word of the solve
+    // Extra e4m3 copy of the output (FP8 experiment): fscale * v, saturated, same
+    // orientation as the output (mirrored for symmetric products); f0 == null: none.
+    void *f0;
+    int64_t ldf;
+    float fscale;
+    int pad_f;
 };
 
 // Per-call arguments of one matrix, read by the kernels of a grouped launch
@@ -114,6 +120,7 @@ struct TcProblem {
     int nseg;
     int segL[3], segR[3];
     int M, N, K;
+    int fp8;                         // operands are e4m3 (kind::f8f6f4): 128 of K per k-block
     int sym;                         // upper tiles only, mirrored store (M == N)
     int tiles_m, tiles_n;
     Epi ep;
@@ -230,6 +237,9 @@ int schedule_coeffs(int kind, int iters, double ell0, double delta, double *coef
 // Tensor-map encoders (driver entry point resolved through the runtime).
 // Operand loads: BF16, box 64 (K) x box_rows, 128-byte swizzle.
 bool encode_bf16_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld,
+                     int box_rows);
+// e4m3 operand loads (FP8 experiment): box 128 (K) x box_rows, 128-byte swizzle.
+bool encode_e4m3_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld,
                      int box_rows);
 // Epilogue stores: BF16 (64-byte swizzle) or FP32 (128-byte swizzle), box 32 x 32.
 bool encode_store_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld,

@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI (no GPU): the library loads, exports every
 symbol include/svt.h declares, and its host arithmetic (status names, options,
 workspace sizes, the polynomial schedule) is right."""
+import ctypes
 import re
 import os
 
@@ -53,6 +54,35 @@ def test_reserved_fp8_tier_is_unsupported():
     with pytest.raises(pkg.SVTError) as e:
         pkg.workspace_bytes(64, 64, prec=7)
     assert e.value.status == pkg.binding.ERR_INVALID
+
+
+def test_fp8_experiment_workspace():
+    """svt_workspace_bytes_fp8: the BF16 tier's workspace plus one e4m3 k x k copy for a
+    P-chain policy and four for an S-chain policy; other tiers are rejected."""
+    m, n = 700, 300
+    base = pkg.workspace_bytes(m, n, prec="bf16")
+    assert pkg.workspace_bytes_fp8(m, n) == base
+    p = pkg.workspace_bytes_fp8(m, n, p_steps=[1, 2])
+    s = pkg.workspace_bytes_fp8(m, n, s_steps=[15, 16], s_y2_only=True)
+    both = pkg.workspace_bytes_fp8(m, n, p_steps=[1], s_steps=[15])
+    k = min(m, n)
+    assert k * k <= p - base <= k * (k + 64) + (1 << 20)
+    assert 4 * k * k <= s - base <= 4 * k * (k + 64) + (4 << 20)
+    assert both - base == (p - base) + (s - base)
+    for bad in ("fp32", "fp64"):
+        with pytest.raises(pkg.SVTError) as e:
+            pkg.workspace_bytes_fp8(m, n, p_steps=[1], prec=bad)
+        assert e.value.status == pkg.binding.ERR_INVALID
+    with pytest.raises(ValueError):
+        pkg.fp8_policy(p_steps=[64])
+    out = ctypes.c_size_t(0)
+    o = pkg.make_options(prec="bf16")
+    bad = pkg.fp8_policy(s_steps=[3])
+    bad.reserved = 1
+    assert pkg.lib().svt_workspace_bytes_fp8(m, n, ctypes.byref(o), ctypes.byref(bad),
+                                             ctypes.byref(out)) == pkg.binding.ERR_INVALID
+    assert pkg.lib().svt_workspace_bytes_fp8(m, n, ctypes.byref(o), None,
+                                             ctypes.byref(out)) == pkg.binding.ERR_INVALID
 
 
 @pytest.mark.parametrize("delta", [0.0, 0.01, 1e-4])
