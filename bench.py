@@ -547,7 +547,7 @@ def paper_shapes_extra(ctx_cls, pkg, torch, dev, reps=5):
     return out
 
 
-def serving_extra(ctx_cls, pkg, torch, dev, n_req=200):
+def serving_extra(ctx_cls, pkg, torch, dev, n_req=2000, loads=(0.5, 0.8, 0.95)):
     """Poisson stream through svt_serve_submit / svt_serve_poll: sizes log-uniform
     256-8192 (rounded to powers of two), aspect 1, 2, 1/2, 30 % FP32 tier. Capacity
     is the closed-loop throughput of the same stream (at most 64 requests in flight);
@@ -579,7 +579,7 @@ def serving_extra(ctx_cls, pkg, torch, dev, n_req=200):
         ys.append(y)
         return y
 
-    def run(arrivals, window=64):
+    def run(arrivals, window=64, plan=plan):
         """arrivals None: closed loop with at most `window` requests in flight."""
         import time as _t
         t0 = _t.perf_counter()
@@ -612,14 +612,14 @@ def serving_extra(ctx_cls, pkg, torch, dev, n_req=200):
             raise RuntimeError(f"{failed} serving requests failed")
         return wall, lat
 
-    run(None)  # warm-up: plans and first launches
+    run(None, plan=sorted(set(plan)))  # warm-up: one request of each shape and tier
     wall, lat = run(None)
     cap = len(plan) / wall
     out = {"workload": f"{n_req} requests, sizes log-uniform 256-8192 rounded to powers of two, "
                        "aspect {1,2,1/2}, rank-20 signal + noise, 70% BF16 / 30% FP32 tier, 20 steps",
            "capacity_req_per_s": cap, "loads": []}
     import random as _r
-    for load in (0.5, 0.8, 0.95):
+    for load in loads:
         rate = load * cap
         rng = _r.Random(1005)
         t, arr = 0.0, []
@@ -630,7 +630,9 @@ def serving_extra(ctx_cls, pkg, torch, dev, n_req=200):
         out["loads"].append({"offered": load, "rate_req_per_s": rate,
                              "throughput_req_per_s": len(plan) / wall,
                              "p50_ms": lat[len(lat) // 2],
-                             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]})
+                             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                             "p999_ms": lat[min(len(lat) - 1, int(0.999 * len(lat)))],
+                             "max_ms": lat[-1]})
     return out
 
 
@@ -927,7 +929,7 @@ def main():
     ap.add_argument("--tile", type=int, default=0, choices=[0, 128, 256, 512],
                     help="product tiles: 0 automatic, 128/256 one CTA per 128 x tile, "
                          "512 a CTA pair per 256 x 256 tile")
-    ap.add_argument("--serve-requests", type=int, default=200,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests per serving run (the serving configuration asks for 10^4)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batch and serving measurements")

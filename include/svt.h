@@ -234,7 +234,10 @@ svt_status svt_batch_workspace_bytes(const svt_matrix *mats, int count, size_t *
  * completes) into the admission queue and returns a ticket. A scheduler thread
  * admits queued requests while their workspaces fit in the context's workspace
  * and a slot is free, advances all admitted requests one stage window at a time
- * with one grouped launch per window, and retires finished requests.
+ * with one grouped launch per window, and retires finished requests. Requests of
+ * at least 8 Mi elements take the large lane instead, one at a time: a fused solve
+ * issued as consecutive launches of a few milliseconds each, on every SM while no
+ * smaller request is waiting or running and on all but 32 SMs otherwise.
  * Errors: SVT_ERR_INVALID (bad request), SVT_ERR_OOM (request larger than the
  * whole workspace), SVT_ERR_BUSY (queue full).
  */
@@ -254,12 +257,13 @@ svt_status svt_serve_release(svt_ctx_t ctx, uint64_t ticket);
 /*
  * Cancel a serving request. A request still in the admission queue is removed at
  * once; one whose stages are being issued window by window is dropped before its
- * next window and retired once its work already on the device has finished. Either
+ * next window and retired once its work already on the device has finished; a large
+ * request is dropped the same way before its next launch. Either
  * way the ticket then polls as SVT_ERR_CANCELLED and its Y is unspecified (the
  * combine that writes Y may or may not have run). Returns SVT_OK when the request
  * is or will be cancelled, SVT_ERR_BUSY when its remaining work is already on the
- * device (a large request's single fused launch, or a small one whose last stage
- * went out: poll for its result), SVT_ERR_INVALID for an unknown or completed
+ * device (its last stage or launch went out, or it is an FP64-tier large request,
+ * issued whole: poll for its result), SVT_ERR_INVALID for an unknown or completed
  * ticket.
  */
 svt_status svt_serve_cancel(svt_ctx_t ctx, uint64_t ticket);

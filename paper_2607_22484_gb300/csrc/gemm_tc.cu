@@ -1125,7 +1125,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const int total = *skip_flag ? 0 : (L.gtab ? L.gstart[L.gcount] : L.tile_start[L.nprob]);
+    const int total = *skip_flag ? 0
+                                 : (L.gtab ? (L.tile_hi > 0 ? L.tile_hi : L.gstart[L.gcount])
+                                           : L.tile_start[L.nprob]);
     // Static schedule (non-fused launches): CTA (pair) i takes tiles i, i + grid, ...
     const int t_first = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
     const int t_step = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
@@ -1150,7 +1152,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                     // other roles (and to the peer CTA of a pair).
                     if (!wait_bar<PAIR>(&rempty[ri], rphase ^ 1u, abort_flag, status0, kWaitTimeoutNs))
                         break;
-                    t = atomicAdd(L.tile_counter, 1);
+                    t = L.tile_lo + atomicAdd(L.tile_counter, 1);
                     t = (t < total) ? t : -1;
                     tc = TileCoord{-1, 0, 0, false};
                     if (t >= 0)

@@ -132,6 +132,11 @@ struct Plan {
     TcLaunch fused_launch;
     int fused_tiles = 0, fused_bn = 0;
     double fused_flops = 0.0;
+    // Table order of the fused solve: first tile of each problem, then the tile count;
+    // the tensor flops of each problem; the op range of the products in `ops`.
+    std::vector<int> fused_starts;
+    std::vector<double> fused_work;
+    size_t fused_first_op = 0, fused_last_op = 0;
     // The fused table lives in the shared workspace, which other solves overwrite:
     // it is copied from this immutable pinned host image before every fused launch.
     uint8_t *h_fused = nullptr;
@@ -272,6 +277,25 @@ svt_status plan_for_solve(svt_ctx *ctx, int64_t m, int64_t n, const Resolved &r,
                           std::shared_ptr<Plan> *keep = nullptr);
 // Refresh the plan's fused-launch table in the workspace from its host image (async on s).
 svt_status upload_fused_table(svt_ctx *ctx, Plan &P, cudaStream_t s);
+// A solve split into consecutive parts of about `target` tensor flops each (at most
+// kMaxFusedSegments). A fused plan splits its product table into contiguous problem
+// ranges (`bounds`: the first problem of each part, then the problem count), each part
+// one launch of the fused kernel over its tiles; a plan issued launch by launch splits
+// its op list (`bounds`: op indices). `work`: the tensor flops of each part.
+struct Segments {
+    bool fused = false;
+    std::vector<int> bounds;
+    std::vector<double> work;
+    int count() const { return (int)bounds.size() - 1; }
+};
+Segments plan_segments(const Plan &P, double target);
+// Issues part k of a solve split by plan_segments on stream s with grids of `sms` SMs.
+// Fused: with k == 0 first the ops before the products (scratch reset, ingest) and the
+// table upload, then the launch over the part's tiles, and with the last part the ops
+// after the products. Parts must be issued in order, each after the previous one on the
+// same stream: the dependency counters carry over between them.
+svt_status run_plan_segment(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s,
+                            const Segments &seg, int k, int sms);
 // Release the context's cached completion graphs (after the device is idle).
 void completion_release(svt_ctx *ctx);
 void serve_shutdown(svt_ctx *ctx);

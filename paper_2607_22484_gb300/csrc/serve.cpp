@@ -48,13 +48,21 @@ namespace {
 
 constexpr int kStreams = 8;
 constexpr int kSlots = 16;
-// Two lanes share the SMs. Requests of at least kLargeElems elements run as one fused
-// persistent solve each (the large lane, one at a time, at most num_sms - kSmallSms
-// SMs); smaller ones advance stage by stage in windows (the small lane), whose
-// grids shrink to kSmallSms while a large solve runs. A large solve then never
-// holds up the short windows, and large requests keep the efficient fused path.
+// Two lanes share the SMs. Requests of at least kLargeElems elements take the large
+// lane; smaller ones advance stage by stage in windows (the small lane), whose grids
+// shrink to kSmallSms while large work runs. A large solve is issued as consecutive
+// launches over parts of its product table (plan_segments) of about kSegmentWork
+// tensor flops each, a few milliseconds, at most two in flight; each takes every SM
+// while the small lane is idle and leaves kSmallSms free while it has work. Up to
+// kMaxLarge large requests are admitted at once, and each launch goes to the admitted
+// one with the least work left (shortest remaining work first): a 4096 x 2048 request
+// does not wait for a 200 ms FP32-tier 8192^2 solve to finish, and a small request
+// waits at most for the launch in progress, never for a whole large solve. The large
+// lane, which carries nearly all of the work, keeps the whole GPU while it runs alone.
 constexpr int64_t kLargeElems = (int64_t)8 << 20;
 constexpr int kSmallSms = 32;
+constexpr double kSegmentWork = 6e12;
+constexpr int kMaxLarge = 4;
 constexpr size_t kQueueLimit = 1 << 16;
 
 // Optional scheduler trace: with SVT_SERVE_TRACE=<file> in the environment, one line
@@ -135,7 +143,8 @@ struct Request {
     size_t ws_len = 0, ws_off = 0;
     int slot = -1;
     double t_submit = 0, t_admit = 0, t_done = 0;
-    int state = 0;  // 0 queued, 1 running (ops being issued), 3 all issued, 2 done
+    int state = 0;  // 0 queued, 1 running (ops being issued), 4 large solve between
+                    // launches, 3 all issued, 2 done
     bool cancel = false;     // svt_serve_cancel on a running request: drop before next window
     bool cancelled = false;  // retire as SVT_ERR_CANCELLED once its issued work is done
     svt_status result = SVT_OK;
@@ -143,7 +152,20 @@ struct Request {
     std::shared_ptr<Plan> plan_ref;  // keeps the plan alive while ops are in flight
     size_t pc = 0;          // next op of the plan to issue
     bool grouped = false;   // ops limited to the kinds the grouped kernels cover
-    bool large = false;     // large lane: one fused solve
+    bool large = false;     // large lane
+    double est_work = 0.0;  // large lane: m n min(m, n), times 3 in the FP32 tier
+    Segments seg;           // large lane: the solve's launches (plan_segments)
+    int seg_next = 0;       // next of them to issue
+    double seg_total = 0.0;
+    double remaining() const  // estimated work not yet issued
+    {
+        if (seg.count() <= 0 || seg_total <= 0.0)
+            return seg_next > 0 ? 0.0 : est_work;
+        double left = 0.0;
+        for (int k = seg_next; k < seg.count(); ++k)
+            left += seg.work[k];
+        return est_work * left / seg_total;
+    }
 };
 
 // Device tables of one serving window live in a ring of slots at the end of the
@@ -227,8 +249,10 @@ struct ServeState {
     uint64_t next_ticket = 1;
     std::deque<Request *> queue;   // small lane, arrival order
     std::deque<Request *> bigq;    // large lane, arrival order
-    Request *big = nullptr;        // the large solve in flight
+    std::vector<Request *> bigs;   // admitted large requests, launches being issued or in flight
     cudaStream_t big_stream = nullptr;
+    cudaEvent_t seg_ev[2] = {};    // the large lane's launch k done (slot k % 2)
+    uint64_t big_issued = 0;       // large-lane launches issued
     std::list<Request *> active;
     std::map<uint64_t, Request *> tickets;
     Arena arena;
@@ -269,6 +293,9 @@ svt_status start_workers(svt_ctx *ctx, ServeState *s)
         return SVT_ERR_CUDA;
     if (!s->big_stream && cudaStreamCreateWithFlags(&s->big_stream, cudaStreamNonBlocking) != cudaSuccess)
         return SVT_ERR_CUDA;
+    for (int i = 0; i < 2; ++i)
+        if (!s->seg_ev[i] && cudaEventCreateWithFlags(&s->seg_ev[i], cudaEventDisableTiming) != cudaSuccess)
+            return SVT_ERR_CUDA;
     if (!s->h_ring && cudaMallocHost(reinterpret_cast<void **>(&s->h_ring), kRingBytes) != cudaSuccess)
         return SVT_ERR_CUDA;
     for (int i = 0; i < kRing; ++i)
@@ -575,62 +602,121 @@ bool tick(svt_ctx *ctx, ServeState *s)
                                       : (r->cancelled ? SVT_ERR_CANCELLED
                                                       : (svt_status)s->h_status[r->slot]));
         trace("done", r->ticket, (long long)r->result);
-        if (r == s->big)
-            s->big = nullptr;
+        if (r->large)
+            s->bigs.erase(std::remove(s->bigs.begin(), s->bigs.end(), r), s->bigs.end());
         it = s->active.erase(it);
         progress = true;
     }
-    // Large lane: the oldest large request runs as one fused solve once no other one
-    // runs and its workspace fits. While it waits for workspace no new small request
-    // is admitted (the running ones free theirs within milliseconds).
+    // Large lane admission: the queued large request with the least work (the oldest of
+    // equals) once fewer than kMaxLarge run and its workspace fits. While it waits for
+    // workspace no new small request is admitted (the running ones free theirs within
+    // milliseconds).
     bool hold_small = false;
     const double t_tick = now_ms();
-    if (!s->big && !s->bigq.empty() && (int)s->active.size() < kSlots &&
-        admissible(ctx, s->bigq.front(), t_tick)) {
-        Request *r = s->bigq.front();
+    while ((int)s->bigs.size() < kMaxLarge && !s->bigq.empty() && (int)s->active.size() < kSlots) {
+        auto pick = s->bigq.end();
+        for (auto it = s->bigq.begin(); it != s->bigq.end(); ++it)
+            if (admissible(ctx, *it, t_tick) && (pick == s->bigq.end() || (*it)->est_work < (*pick)->est_work))
+                pick = it;
+        if (pick == s->bigq.end())
+            break;
+        Request *r = *pick;
         size_t off;
         if (!s->arena.alloc(r->ws_len, &off)) {
-            hold_small = true;
+            hold_small = s->bigs.empty();
             trace("hold", r->ticket, (long long)r->ws_len);
-        } else {
-            s->bigq.pop_front();
-            const double t0 = trace_file() ? now_ms() : 0.0;
-            int slot = 0;
-            while (s->slot_used[slot])
-                ++slot;
-            s->slot_used[slot] = true;
-            r->slot = slot;
-            r->ws_off = off;
-            r->t_admit = now_ms();
-            Plan *plan = nullptr;
-            svt_status e;
-            {
-                std::lock_guard<std::mutex> g(ctx->mu);
-                NvtxRange nvtx("svt serve large launch");
-                evict_plans(ctx, 512);
-                e = get_plan(ctx, r->m.m, r->m.n, r->opt, off, ctx->ws_bytes - kRingBytes - off,
-                             &plan, 0, &r->plan_ref);
-                if (e == SVT_OK) {
-                    CallArgs a{r->m.A, r->m.lda, r->m.tau, r->m.Y, r->m.ldy, r->m.d_status};
-                    e = run_plan(ctx, *plan, a, s->big_stream, ctx->num_sms - kSmallSms);
-                }
-                if (e == SVT_OK)
-                    e = plan_status_copy(ctx, *plan, &s->h_status[slot], s->big_stream);
-            }
-            if (e == SVT_OK && cudaEventRecord(s->events[slot], s->big_stream) != cudaSuccess)
-                e = SVT_ERR_CUDA;
-            trace("large_launch", r->ticket, trace_file() ? (long long)((now_ms() - t0) * 1e3) : 0);
-            if (e != SVT_OK) {
-                cudaStreamSynchronize(s->big_stream);
-                finish(s, r, e);
-            } else {
-                r->plan = plan;
-                r->state = 3;
-                s->active.push_back(r);
-                s->big = r;
-            }
-            progress = true;
+            break;
         }
+        s->bigq.erase(pick);
+        const double t0 = trace_file() ? now_ms() : 0.0;
+        int slot = 0;
+        while (s->slot_used[slot])
+            ++slot;
+        s->slot_used[slot] = true;
+        r->slot = slot;
+        r->ws_off = off;
+        r->t_admit = now_ms();
+        Plan *plan = nullptr;
+        svt_status e;
+        {
+            std::lock_guard<std::mutex> g(ctx->mu);
+            NvtxRange nvtx("svt serve large admit");
+            evict_plans(ctx, 512);
+            e = get_plan(ctx, r->m.m, r->m.n, r->opt, off, ctx->ws_bytes - kRingBytes - off, &plan, 0,
+                         &r->plan_ref);
+            if (e == SVT_OK) {
+                r->seg = plan_segments(*plan, kSegmentWork);
+                r->seg_next = 0;
+                r->seg_total = 0.0;
+                for (double w : r->seg.work)
+                    r->seg_total += w;
+            }
+        }
+        trace("large_admit", r->ticket, trace_file() ? (long long)((now_ms() - t0) * 1e3) : 0);
+        if (e != SVT_OK) {
+            finish(s, r, e);
+        } else {
+            r->plan = plan;
+            r->state = 4;
+            s->active.push_back(r);
+            s->bigs.push_back(r);
+        }
+        progress = true;
+    }
+    // Large lane launches: at most two in flight; each to the admitted request with the
+    // least work left; every SM while no small request waits or runs.
+    for (;;) {
+        Request *r = nullptr;
+        for (Request *q : s->bigs)
+            if (q->state == 4 && q->cancel) {  // dropped before its next launch
+                if (cudaEventRecord(s->events[q->slot], s->big_stream) != cudaSuccess)
+                    continue;  // retried next tick
+                q->state = 3;
+                q->cancelled = true;
+                trace("cancel", q->ticket, (long long)q->seg_next);
+                progress = true;
+            }
+        for (Request *q : s->bigs)
+            if (q->state == 4 && (!r || q->remaining() < r->remaining()))
+                r = q;
+        if (!r)
+            break;
+        const uint64_t k = s->big_issued;
+        if (k >= 2 && cudaEventQuery(s->seg_ev[k % 2]) == cudaErrorNotReady)
+            break;
+        bool small_busy = !s->queue.empty();
+        for (Request *q : s->active)
+            small_busy = small_busy || !q->large;
+        const int width = small_busy ? ctx->num_sms - kSmallSms : ctx->num_sms;
+        const int part = r->seg_next;
+        const bool last = part == r->seg.count() - 1;
+        svt_status e;
+        {
+            std::lock_guard<std::mutex> g(ctx->mu);
+            NvtxRange nvtx("svt serve large launch");
+            CallArgs a{r->m.A, r->m.lda, r->m.tau, r->m.Y, r->m.ldy, r->m.d_status};
+            e = run_plan_segment(ctx, *r->plan, a, s->big_stream, r->seg, part, width);
+            if (e == SVT_OK && cudaEventRecord(s->seg_ev[k % 2], s->big_stream) != cudaSuccess)
+                e = SVT_ERR_CUDA;
+            if (e == SVT_OK && last) {
+                e = plan_status_copy(ctx, *r->plan, &s->h_status[r->slot], s->big_stream);
+                if (e == SVT_OK && cudaEventRecord(s->events[r->slot], s->big_stream) != cudaSuccess)
+                    e = SVT_ERR_CUDA;
+            }
+        }
+        trace("large_launch", r->ticket, (long long)part * 1000 + width);
+        progress = true;
+        s->big_issued = k + 1;
+        if (e != SVT_OK) {
+            cudaStreamSynchronize(s->big_stream);
+            s->active.remove(r);
+            s->bigs.erase(std::remove(s->bigs.begin(), s->bigs.end(), r), s->bigs.end());
+            finish(s, r, e);
+            continue;
+        }
+        r->seg_next = part + 1;
+        if (last)
+            r->state = 3;
     }
     // Small lane: admit in arrival order while a slot and workspace are free.
     while (!hold_small && !s->queue.empty() && (int)s->active.size() < kSlots &&
@@ -688,7 +774,7 @@ bool tick(svt_ctx *ctx, ServeState *s)
     if (any) {
         const double t0 = trace_file() ? now_ms() : 0.0;
         NvtxRange nvtx("svt serve window");
-        svt_status e = issue_window(ctx, s, s->big ? kSmallSms : ctx->num_sms);
+        svt_status e = issue_window(ctx, s, s->bigs.empty() ? ctx->num_sms : kSmallSms);
         if (e == SVT_ERR_NOT_READY)
             return progress;
         trace("window", s->windows, trace_file() ? (long long)((now_ms() - t0) * 1e3) : 0);
@@ -972,6 +1058,9 @@ void serve_shutdown(svt_ctx *ctx)
     for (int i = 0; i < kRing; ++i)
         if (s->ring_ev[i])
             cudaEventDestroy(s->ring_ev[i]);
+    for (int i = 0; i < 2; ++i)
+        if (s->seg_ev[i])
+            cudaEventDestroy(s->seg_ev[i]);
     if (s->h_ring)
         cudaFreeHost(s->h_ring);
     if (s->metrics)
@@ -1267,6 +1356,8 @@ svt_status svt_serve_submit(svt_ctx_t ctx, const svt_matrix *req, uint64_t *tick
     q->ws_len = need;
     q->t_submit = now_ms();
     q->large = large;
+    q->est_work = (double)req->m * (double)req->n * (double)std::min(req->m, req->n) *
+                  (r.prec == SVT_FP32 ? 3.0 : 1.0);
     (large ? s->bigq : s->queue).push_back(q);
     trace("submit", q->ticket, large ? 1 : 0);
     s->tickets[q->ticket] = q;
@@ -1314,6 +1405,7 @@ svt_status svt_serve_cancel(svt_ctx_t ctx, uint64_t ticket)
         return SVT_OK;
     }
     case 1:  // stages being issued: the scheduler drops it before its next window
+    case 4:  // large solve between launches: dropped before its next launch
         r->cancel = true;
         s->cv.notify_all();
         return SVT_OK;

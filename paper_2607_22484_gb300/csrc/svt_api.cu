@@ -234,7 +234,8 @@ Layout make_layout(int64_t m, int64_t n, const Resolved &r)
     L.status = a.take(sizeof(int) * 4);
     // Product launches of a solve: Gram, 3 per step, 2 polish, combine; <= 2 problems each.
     L.max_problems = 2 * (1 + 3 * std::max(0, r.iters) + 2 + 1);
-    L.counters = a.take(sizeof(int) * (size_t)(L.max_problems + 1));  // done[], tile counter
+    // done[] and one tile counter per launch of a fused solve
+    L.counters = a.take(sizeof(int) * (size_t)(L.max_problems + kMaxFusedSegments));
     L.colnorm = a.take((size_t)L.N * sizeof(double));
     const bool pairs = fp32;  // iterates carried as hi/lo pairs
     for (int i = 0; i < 2; ++i) {
@@ -1013,6 +1014,84 @@ svt_status run_plan(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s, in
     return run_ops(ctx, P, a, s, 0, P.ops.size(), sms);
 }
 
+Segments plan_segments(const Plan &P, double target)
+{
+    Segments seg;
+    seg.fused = P.fused;
+    // Work of each unit: a problem of the fused table, or an op of the plan.
+    std::vector<double> unit;
+    if (P.fused) {
+        unit = P.fused_work;
+    } else {
+        for (const Op &op : P.ops)
+            unit.push_back(op.kind == OP_TC ? P.tc_tensor_flops[op.idx] : 0.0);
+    }
+    const int nu = (int)unit.size();
+    if (nu == 0) {
+        seg.bounds = {0, 0};
+        seg.work = {0.0};
+        return seg;
+    }
+    double total = 0.0;
+    for (double w : unit)
+        total += w;
+    const int want =
+        (int)std::min<double>(kMaxFusedSegments, std::max(1.0, std::ceil(total / std::max(target, 1.0))));
+    const double per = total / want;
+    seg.bounds.push_back(0);
+    seg.work.push_back(0.0);
+    double acc = 0.0;
+    for (int i = 0; i < nu; ++i) {
+        acc += unit[i];
+        seg.work.back() += unit[i];
+        if (acc >= per * (double)seg.bounds.size() && i + 1 < nu && (int)seg.bounds.size() < want) {
+            seg.bounds.push_back(i + 1);
+            seg.work.push_back(0.0);
+        }
+    }
+    seg.bounds.push_back(nu);
+    return seg;
+}
+
+svt_status run_plan_segment(svt_ctx *ctx, Plan &P, const CallArgs &a, cudaStream_t s,
+                            const Segments &seg, int k, int sms)
+{
+    const int nseg = seg.count();
+    if (k < 0 || k >= nseg || nseg > kMaxFusedSegments || a.in_graph || seg.fused != P.fused)
+        return SVT_ERR_INVALID;
+    if (!seg.fused)
+        return run_ops(ctx, P, a, s, (size_t)seg.bounds[k], (size_t)seg.bounds[k + 1], sms);
+    svt_status st;
+    if (k == 0) {
+        if ((st = run_ops(ctx, P, a, s, 0, P.fused_first_op, sms)) != SVT_OK)
+            return st;
+        if ((st = upload_fused_table(ctx, P, s)) != SVT_OK)
+            return st;
+    }
+    TcLaunch l = P.fused_launch;
+    l.dep_wait_ns = ctx->dbg_wait_ns;
+    l.call_inline.A = a.A;
+    l.call_inline.Y = a.Y;
+    l.call_inline.lda = a.lda;
+    l.call_inline.ldy = a.ldy;
+    l.call_inline.tau = a.tau;
+    l.call_inline.d_status = a.d_status;
+    l.tile_lo = P.fused_starts[seg.bounds[k]];
+    l.tile_hi = P.fused_starts[seg.bounds[k + 1]];
+    l.tile_counter = P.fused_launch.tile_counter + k;  // zeroed with the solve's scratch
+    const int grid_sms = (sms > 0 && sms < ctx->num_sms) ? sms : ctx->num_sms;
+    if (l.tile_hi > l.tile_lo) {
+        cudaError_t err = tc_gemm_launch_fused(l, P.fused_bn, l.tile_hi - l.tile_lo, grid_sms, s,
+                                               P.uses_strips);
+        ctx->launches += 1;
+        if (err != cudaSuccess)
+            return SVT_ERR_CUDA;
+    }
+    if (k == nseg - 1)
+        return run_ops(ctx, P, a, s, P.fused_last_op + 1, P.ops.size(), sms);
+    return SVT_OK;
+}
+
 namespace {
 
 // One persistent launch for all products of the plan: problems in program order,
@@ -1049,6 +1128,7 @@ svt_status build_fused(svt_ctx *ctx, Plan &P)
     std::vector<TcProblem> probs;
     std::vector<DepProduct> dps;
     std::vector<int> starts;
+    std::vector<double> work;
     size_t ci = 0;
     int total = 0;
     for (size_t i = first; i <= last; ++i) {
@@ -1070,6 +1150,9 @@ svt_status build_fused(svt_ctx *ctx, Plan &P)
                            tp.tiles_n, tc_valid_ctas(tp, bn), io.theta_src, io.norm_acc, io.f});
             starts.push_back(total);
             total += tc_num_tiles(tp, bn);
+            const int kb = tp.fp8 ? 2 * kBK : kBK;
+            work.push_back((double)tp.nseg * (double)tc_valid_ctas(tp, bn) * 2.0 * kBM *
+                           (double)tile_cols(bn) * (double)((tp.K + kb - 1) / kb * kb));
             probs.push_back(tp);
         }
     }
@@ -1123,6 +1206,10 @@ svt_status build_fused(svt_ctx *ctx, Plan &P)
     P.fused_launch.strips = reinterpret_cast<int *>(base + P.lay.strips);
     P.fused_tiles = total;
     P.fused_bn = bn;
+    P.fused_starts = starts;
+    P.fused_work = work;
+    P.fused_first_op = first;
+    P.fused_last_op = last;
     P.fused_flops = 0.0;
     for (double f : P.tc_flops)
         P.fused_flops += f;

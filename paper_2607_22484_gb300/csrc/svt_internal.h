@@ -21,6 +21,7 @@
 namespace svt {
 
 constexpr int kMaxProblems = 2;   // problems per by-value grouped launch (P and S chains)
+constexpr int kMaxFusedSegments = 64;  // launches a fused solve may be split into
 constexpr int kBM = 128;          // tile rows (tcgen05 M)
 constexpr int kBK = 64;           // K per pipeline stage: one 128-byte swizzle row of BF16
 
@@ -140,6 +141,9 @@ struct TcLaunch {
     // (tile, epilogue warp) pairs. Both live in the solve's zeroed scratch.
     int *tile_counter;
     int *done;
+    // Fused launches over part of the table (a segment of a solve issued as several
+    // launches): tiles [tile_lo, tile_hi) in table order; tile_hi == 0: the whole table.
+    int tile_lo, tile_hi;
     int *strips;  // fused solves: per-problem strip completion counters
     CallRec call_inline;             // per-call fields when calls == nullptr
     // Limit of the waits on other tiles' results (dependency counters), ns; 0: the

@@ -198,3 +198,48 @@ def test_tuning_cache_roundtrip_and_gpu_key():
             fresh.tuning_import(bad)
         assert err.value.status == B.ERR_INVALID
     assert json.loads(fresh.tuning_export())["entries"] == []
+
+
+def test_large_lane_alone_and_cancel_between_launches(tmp_path):
+    """A large request (at least 8 Mi elements) is issued as consecutive fused launches
+    over parts of its product table: alone it runs them on every SM and equals the same
+    solve through svt_polar; cancelled while its launches are being issued it stops
+    before the next one and polls SVT_ERR_CANCELLED (or, were it already fully issued,
+    the cancel answers SVT_ERR_BUSY and the result is normal), and the context keeps
+    serving."""
+    log = tmp_path / "large.jsonl"
+    ctx = pkg.Context(0, workspace_bytes=pkg.workspace_bytes(8192, 4096, prec="fp32") + (256 << 20))
+    ctx.serve_metrics(log)
+    a = torch.from_numpy(_gap_matrix(4096, 2048, seed=61)).cuda()
+    y = torch.full_like(a, float("nan"))
+    torch.cuda.synchronize()
+    for _ in range(2):  # the first submission builds the plan
+        t = ctx.submit(a, 0.3, y, iters=20, prec="bf16")
+        assert _wait(ctx, [t])[t][0] == B.OK
+        assert ctx.release(t) == B.OK
+    ref = pkg.Context(0, workspace_bytes=1 << 20).polar(a, 0.3, iters=20, prec="bf16")
+    torch.cuda.synchronize()
+    assert oracle.relerr(y.cpu().numpy(), ref.cpu().numpy()) < 1e-5
+
+    big = torch.from_numpy(_gap_matrix(8192, 4096, seed=62)).cuda()
+    ybig = torch.empty_like(big)
+    small = torch.from_numpy(_gap_matrix(256, 192, seed=63)).cuda()
+    ysmall = torch.empty_like(small)
+    torch.cuda.synchronize()
+    tb = ctx.submit(big, 0.3, ybig, iters=20, prec="fp32")  # about 100 ms of launches
+    time.sleep(0.02)
+    rc = ctx.cancel(tb)
+    res = _wait(ctx, [tb])
+    if rc == B.OK:
+        assert res[tb][0] == B.ERR_CANCELLED
+    else:
+        assert rc == B.ERR_BUSY and res[tb][0] == B.OK
+    print(f"cancel of a running 8192 x 4096 FP32-tier request after 20 ms: {pkg.status_str(rc)}")
+    ts = ctx.submit(small, 0.3, ysmall, iters=20, prec="bf16")
+    assert _wait(ctx, [ts])[ts][0] == B.OK
+    exact = oracle.svt_definition(small.cpu().numpy().astype(np.float64), 0.3)
+    assert oracle.relerr(ysmall.cpu().numpy(), exact) < 2e-2
+    ctx.serve_metrics(None)
+    recs = {r["ticket"]: r for r in map(json.loads, log.read_text().splitlines())}
+    assert recs[tb]["lane"] == "large" and recs[ts]["lane"] == "small"
+    assert recs[tb]["status"] == pkg.status_str(res[tb][0])
