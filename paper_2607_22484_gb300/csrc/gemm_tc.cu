@@ -993,6 +993,119 @@ __device__ __forceinline__ void epilogue_finish(const EpiHot &h, int64_t r0, int
     __syncwarp();
 }
 
+// Product kinds whose epilogue runs a specialised chunk loop (chosen once per tile):
+// BF16 output through TMA stores, no norm, no FP64 diagonal, no e4m3 copy, and
+//   kSpecSym  : symmetric, no C               (Y = X^T X, Y = S^2, S Z)
+//   kSpecSymC : symmetric, C in BF16          (Z = a I + b Y + c Y^2)
+//   kSpecT    : general, transposed BF16 copy (X Z and its X^T)
+// Everything else runs the generic loop (kSpecGeneric).
+constexpr int kSpecGeneric = -1, kSpecSym = 0, kSpecSymC = 1, kSpecT = 2;
+
+template <int S>
+struct EpiSpec {
+    static constexpr bool generic = S == kSpecGeneric;
+    static constexpr bool sym = S == kSpecSym || S == kSpecSymC;
+    static constexpr bool has_c = S == kSpecSymC;
+    static constexpr bool has_t = S == kSpecT;
+};
+
+__device__ __forceinline__ int epi_spec(const EpiHot &h)
+{
+    if (h.o_kind != O_BF16 || !h.otma || h.o_trans || h.norm_acc || h.f0 || h.diag)
+        return kSpecGeneric;
+    if (h.sym && h.t_kind == O_NONE) {
+        if (h.c_kind == C_NONE)
+            return kSpecSym;
+        if (h.c_kind == C_BF16 && !h.c_trans)
+            return kSpecSymC;
+        return kSpecGeneric;
+    }
+    if (!h.sym && h.t_kind == O_BF16 && h.ttma && h.c_kind == C_NONE && h.gamma == 0.f)
+        return kSpecT;
+    return kSpecGeneric;
+}
+
+// c_load / c_apply for a BF16, untransposed C.
+__device__ __forceinline__ bool c_load_bf16(const EpiHot &h, int64_t r, int64_t c0, bool full_row,
+                                            CRaw &cr)
+{
+    if (!full_row)
+        return false;
+    const __nv_bfloat16 *ph = static_cast<const __nv_bfloat16 *>(h.c0) + r * h.ldc + c0;
+    if (!aligned16(ph))
+        return false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        cr.q[q] = __ldg(reinterpret_cast<const uint4 *>(ph) + q);
+    return true;
+}
+
+__device__ __forceinline__ void c_apply_bf16(const EpiHot &h, const CRaw &cr, bool vec, int64_t r,
+                                             int64_t c0, int ncol, bool row_ok, float *v)
+{
+    if (!row_ok)
+        return;
+    const float beta = h.beta;
+    if (vec) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&cr.q[q]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 f = __bfloat1622float2(b[j]);
+                v[q * 8 + 2 * j] += beta * f.x;
+                v[q * 8 + 2 * j + 1] += beta * f.y;
+            }
+        }
+        return;
+    }
+    const __nv_bfloat16 *p = static_cast<const __nv_bfloat16 *>(h.c0) + r * h.ldc + c0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        if (i < ncol)
+            v[i] += beta * __bfloat162float(p[i]);
+}
+
+// epilogue_finish for the specialised kinds: the identity term on the diagonal of a
+// symmetric product, then TMA stores of the block, its mirror (symmetric, off the
+// diagonal) or its transposed copy; diagonal blocks of symmetric products are stored
+// whole from shared memory with their upper triangle mirrored, as in the generic path.
+template <int NSTG, bool SYM, bool HAST>
+__device__ __forceinline__ void epilogue_finish_bf16(const EpiHot &h, int64_t r0, int64_t c0,
+                                                     float *v, uint8_t *stg, int &slot, int lane)
+{
+    if (SYM) {
+        if (r0 == c0) {
+            const float g = h.gamma;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if (i == lane)
+                    v[i] += g;
+            if (lane == 0)
+                bulk_wait_read0();
+            __syncwarp();
+            float *st = reinterpret_cast<float *>(stg);
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                st[xs_idx(lane, i)] = v[i];
+            __syncwarp();
+            store_block(st, O_BF16, h.o0, nullptr, h.ldo, r0, c0, h.M, h.N, false, true, lane);
+            __syncwarp();
+            return;
+        }
+        tma_store_block<NSTG>(v, O_BF16, false, &h.maps[0], &h.maps[1], (int)r0, (int)c0, stg, slot,
+                              lane);
+        tma_store_block<NSTG>(v, O_BF16, true, &h.maps[0], &h.maps[1], (int)r0, (int)c0, stg, slot,
+                              lane);
+        return;
+    }
+    tma_store_block<NSTG>(v, O_BF16, false, &h.maps[0], &h.maps[1], (int)r0, (int)c0, stg, slot,
+                          lane);
+    if (HAST)
+        tma_store_block<NSTG>(v, O_BF16, true, &h.maps[2], &h.maps[3], (int)r0, (int)c0, stg, slot,
+                              lane);
+}
+
 // Load the epilogue fields of problem P (with the per-call fields of a grouped or
 // fused launch) into registers.
 __device__ __forceinline__ void load_hot(EpiHot &h, const TcProblem &P, const CallRec *calls)
@@ -1379,6 +1492,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         int buf = 0;
         uint32_t tphase = 0;
         int last_prob = -1;
+        int spec = kSpecGeneric;
         bool c_done = true;
         EpiHot h;
         int ri = 0;
@@ -1447,6 +1561,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 tc.tm = 2 * tc.tm + (int)rank;  // this CTA's 128-row half of the tile
             if (tc.prob != last_prob) {
                 load_hot(h, P, calls);
+                spec = epi_spec(h);
                 last_prob = tc.prob;
             }
             const int64_t warp_row0 = (int64_t)tc.tm * kBM + quad * 32;
@@ -1475,22 +1590,53 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 break;
             tc_fence_after();
             double nrm = 0.0;
+            // The chunk loop, one copy per product kind (chosen once per tile): the
+            // specialised copies carry no tests of output, C, norm and copy kinds.
+            auto chunk_loop = [&](auto spec_tag) {
+                using Spec = decltype(spec_tag);
 #pragma unroll 1
-            while (ch < BN / 32) {
-                const int nx = next_chunk(ch + 2);
-                const int64_t c0 = (int64_t)tc.tn * BN + ch * 32;
-                const int64_t rem = (int64_t)h.N - c0;
-                float v[32];
-                tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + ch * 32), v);
+                while (ch < BN / 32) {
+                    const int nx = next_chunk(ch + 2);
+                    const int64_t c0 = (int64_t)tc.tn * BN + ch * 32;
+                    const int64_t rem = (int64_t)h.N - c0;
+                    float v[32];
+                    tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + ch * 32),
+                              v);
 #pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    v[i] *= h.alpha;
-                c_apply(h, cr, cvec, row, c0, rem < 32 ? (int)rem : 32, row_ok, v);
-                // The next chunk's C is in flight while this chunk is stored.
-                if (nx < BN / 32)
-                    cvec = c_load(h, row, (int64_t)tc.tn * BN + nx * 32, full_row(nx), cr);
-                epilogue_finish<NSTG>(h, warp_row0, c0, v, nrm, stage_buf, slot, lane);
-                ch = nx;
+                    for (int i = 0; i < 32; ++i)
+                        v[i] *= h.alpha;
+                    if constexpr (Spec::generic) {
+                        c_apply(h, cr, cvec, row, c0, rem < 32 ? (int)rem : 32, row_ok, v);
+                        // The next chunk's C is in flight while this chunk is stored.
+                        if (nx < BN / 32)
+                            cvec = c_load(h, row, (int64_t)tc.tn * BN + nx * 32, full_row(nx), cr);
+                        epilogue_finish<NSTG>(h, warp_row0, c0, v, nrm, stage_buf, slot, lane);
+                    } else {
+                        if constexpr (Spec::has_c) {
+                            c_apply_bf16(h, cr, cvec, row, c0, rem < 32 ? (int)rem : 32, row_ok, v);
+                            if (nx < BN / 32)
+                                cvec = c_load_bf16(h, row, (int64_t)tc.tn * BN + nx * 32, full_row(nx),
+                                                   cr);
+                        }
+                        epilogue_finish_bf16<NSTG, Spec::sym, Spec::has_t>(h, warp_row0, c0, v,
+                                                                           stage_buf, slot, lane);
+                    }
+                    ch = nx;
+                }
+            };
+            switch (spec) {
+            case kSpecSym:
+                chunk_loop(EpiSpec<kSpecSym>{});
+                break;
+            case kSpecSymC:
+                chunk_loop(EpiSpec<kSpecSymC>{});
+                break;
+            case kSpecT:
+                chunk_loop(EpiSpec<kSpecT>{});
+                break;
+            default:
+                chunk_loop(EpiSpec<kSpecGeneric>{});
+                break;
             }
             if (h.norm_acc) {
 #pragma unroll
