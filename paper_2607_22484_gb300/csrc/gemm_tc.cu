@@ -994,53 +994,66 @@ __device__ __forceinline__ void epilogue_finish(const EpiHot &h, int64_t r0, int
 }
 
 // Product kinds whose epilogue runs a specialised chunk loop (chosen once per tile):
-// BF16 output through TMA stores, no norm, no FP64 diagonal, no e4m3 copy, and
-//   kSpecSym  : symmetric, no C               (Y = X^T X, Y = S^2, S Z)
-//   kSpecSymC : symmetric, C in BF16          (Z = a I + b Y + c Y^2)
-//   kSpecT    : general, transposed BF16 copy (X Z and its X^T)
-// Everything else runs the generic loop (kSpecGeneric).
-constexpr int kSpecGeneric = -1, kSpecSym = 0, kSpecSymC = 1, kSpecT = 2;
-
+// BF16 or hi/lo-pair output through TMA stores, no norm, no FP64 diagonal, no e4m3
+// copy, untransposed output, and one of
+//   symmetric, no C                 (Y = X^T X, Y = S^2, S Z)
+//   symmetric, C of the output kind (Z = a I + b Y + c Y^2)
+//   general, no C, transposed copy of the output kind (X Z and its X^T)
+// Everything else runs the generic loop (code -1). Code = 3 * (output is a pair) +
+// (0 symmetric, 1 symmetric with C, 2 general with copy).
 template <int S>
 struct EpiSpec {
-    static constexpr bool generic = S == kSpecGeneric;
-    static constexpr bool sym = S == kSpecSym || S == kSpecSymC;
-    static constexpr bool has_c = S == kSpecSymC;
-    static constexpr bool has_t = S == kSpecT;
+    static constexpr bool generic = S < 0;
+    static constexpr int okind = S >= 3 ? O_PAIR : O_BF16;
+    static constexpr bool sym = S >= 0 && S % 3 != 2;
+    static constexpr int ckind = (S >= 0 && S % 3 == 1) ? (S >= 3 ? C_PAIR : C_BF16) : C_NONE;
+    static constexpr bool has_t = S >= 0 && S % 3 == 2;
 };
 
 __device__ __forceinline__ int epi_spec(const EpiHot &h)
 {
-    if (h.o_kind != O_BF16 || !h.otma || h.o_trans || h.norm_acc || h.f0 || h.diag)
-        return kSpecGeneric;
+    if ((h.o_kind != O_BF16 && h.o_kind != O_PAIR) || !h.otma || h.o_trans || h.norm_acc || h.f0 ||
+        h.diag)
+        return -1;
+    const bool pair = h.o_kind == O_PAIR;
+    const int base = pair ? 3 : 0;
     if (h.sym && h.t_kind == O_NONE) {
         if (h.c_kind == C_NONE)
-            return kSpecSym;
-        if (h.c_kind == C_BF16 && !h.c_trans)
-            return kSpecSymC;
-        return kSpecGeneric;
+            return base;
+        if (h.c_kind == (pair ? C_PAIR : C_BF16) && !h.c_trans)
+            return base + 1;
+        return -1;
     }
-    if (!h.sym && h.t_kind == O_BF16 && h.ttma && h.c_kind == C_NONE && h.gamma == 0.f)
-        return kSpecT;
-    return kSpecGeneric;
+    if (!h.sym && h.t_kind == h.o_kind && h.ttma && h.c_kind == C_NONE && h.gamma == 0.f)
+        return base + 2;
+    return -1;
 }
 
-// c_load / c_apply for a BF16, untransposed C.
-__device__ __forceinline__ bool c_load_bf16(const EpiHot &h, int64_t r, int64_t c0, bool full_row,
+// c_load / c_apply for an untransposed C in BF16 (CK = C_BF16) or as a hi/lo pair.
+template <int CK>
+__device__ __forceinline__ bool c_load_spec(const EpiHot &h, int64_t r, int64_t c0, bool full_row,
                                             CRaw &cr)
 {
     if (!full_row)
         return false;
-    const __nv_bfloat16 *ph = static_cast<const __nv_bfloat16 *>(h.c0) + r * h.ldc + c0;
-    if (!aligned16(ph))
+    const int64_t off = r * h.ldc + c0;
+    const __nv_bfloat16 *ph = static_cast<const __nv_bfloat16 *>(h.c0) + off;
+    const __nv_bfloat16 *pl = static_cast<const __nv_bfloat16 *>(h.c1) + off;
+    if (!aligned16(ph) || (CK == C_PAIR && !aligned16(pl)))
         return false;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         cr.q[q] = __ldg(reinterpret_cast<const uint4 *>(ph) + q);
+    if (CK == C_PAIR) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            cr.q[4 + q] = __ldg(reinterpret_cast<const uint4 *>(pl) + q);
+    }
     return true;
 }
 
-__device__ __forceinline__ void c_apply_bf16(const EpiHot &h, const CRaw &cr, bool vec, int64_t r,
+template <int CK>
+__device__ __forceinline__ void c_apply_spec(const EpiHot &h, const CRaw &cr, bool vec, int64_t r,
                                              int64_t c0, int ncol, bool row_ok, float *v)
 {
     if (!row_ok)
@@ -1048,30 +1061,40 @@ __device__ __forceinline__ void c_apply_bf16(const EpiHot &h, const CRaw &cr, bo
     const float beta = h.beta;
     if (vec) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&cr.q[q]);
+        for (int half = 0; half < (CK == C_PAIR ? 2 : 1); ++half) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float2 f = __bfloat1622float2(b[j]);
-                v[q * 8 + 2 * j] += beta * f.x;
-                v[q * 8 + 2 * j + 1] += beta * f.y;
+            for (int q = 0; q < 4; ++q) {
+                const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&cr.q[4 * half + q]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float2 f = __bfloat1622float2(b[j]);
+                    v[q * 8 + 2 * j] += beta * f.x;
+                    v[q * 8 + 2 * j + 1] += beta * f.y;
+                }
             }
         }
         return;
     }
-    const __nv_bfloat16 *p = static_cast<const __nv_bfloat16 *>(h.c0) + r * h.ldc + c0;
+    const int64_t off = r * h.ldc + c0;
+    const __nv_bfloat16 *ph = static_cast<const __nv_bfloat16 *>(h.c0) + off;
+    const __nv_bfloat16 *pl = static_cast<const __nv_bfloat16 *>(h.c1) + off;
 #pragma unroll
     for (int i = 0; i < 32; ++i)
-        if (i < ncol)
-            v[i] += beta * __bfloat162float(p[i]);
+        if (i < ncol) {
+            float x = __bfloat162float(ph[i]);
+            if (CK == C_PAIR)
+                x += __bfloat162float(pl[i]);
+            v[i] += beta * x;
+        }
 }
 
-// epilogue_finish for the specialised kinds: the identity term on the diagonal of a
-// symmetric product, then TMA stores of the block, its mirror (symmetric, off the
-// diagonal) or its transposed copy; diagonal blocks of symmetric products are stored
-// whole from shared memory with their upper triangle mirrored, as in the generic path.
-template <int NSTG, bool SYM, bool HAST>
-__device__ __forceinline__ void epilogue_finish_bf16(const EpiHot &h, int64_t r0, int64_t c0,
+// epilogue_finish for the specialised kinds (output kind OK): the identity term on the
+// diagonal of a symmetric product, then TMA stores of the block, its mirror (symmetric,
+// off the diagonal) or its transposed copy; diagonal blocks of symmetric products are
+// stored whole from shared memory with their upper triangle mirrored, as in the generic
+// path.
+template <int NSTG, int OK, bool SYM, bool HAST>
+__device__ __forceinline__ void epilogue_finish_spec(const EpiHot &h, int64_t r0, int64_t c0,
                                                      float *v, uint8_t *stg, int &slot, int lane)
 {
     if (SYM) {
@@ -1089,21 +1112,17 @@ __device__ __forceinline__ void epilogue_finish_bf16(const EpiHot &h, int64_t r0
             for (int i = 0; i < 32; ++i)
                 st[xs_idx(lane, i)] = v[i];
             __syncwarp();
-            store_block(st, O_BF16, h.o0, nullptr, h.ldo, r0, c0, h.M, h.N, false, true, lane);
+            store_block(st, OK, h.o0, h.o1, h.ldo, r0, c0, h.M, h.N, false, true, lane);
             __syncwarp();
             return;
         }
-        tma_store_block<NSTG>(v, O_BF16, false, &h.maps[0], &h.maps[1], (int)r0, (int)c0, stg, slot,
-                              lane);
-        tma_store_block<NSTG>(v, O_BF16, true, &h.maps[0], &h.maps[1], (int)r0, (int)c0, stg, slot,
-                              lane);
+        tma_store_block<NSTG>(v, OK, false, &h.maps[0], &h.maps[1], (int)r0, (int)c0, stg, slot, lane);
+        tma_store_block<NSTG>(v, OK, true, &h.maps[0], &h.maps[1], (int)r0, (int)c0, stg, slot, lane);
         return;
     }
-    tma_store_block<NSTG>(v, O_BF16, false, &h.maps[0], &h.maps[1], (int)r0, (int)c0, stg, slot,
-                          lane);
+    tma_store_block<NSTG>(v, OK, false, &h.maps[0], &h.maps[1], (int)r0, (int)c0, stg, slot, lane);
     if (HAST)
-        tma_store_block<NSTG>(v, O_BF16, true, &h.maps[2], &h.maps[3], (int)r0, (int)c0, stg, slot,
-                              lane);
+        tma_store_block<NSTG>(v, OK, true, &h.maps[2], &h.maps[3], (int)r0, (int)c0, stg, slot, lane);
 }
 
 // Load the epilogue fields of problem P (with the per-call fields of a grouped or
@@ -1492,7 +1511,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         int buf = 0;
         uint32_t tphase = 0;
         int last_prob = -1;
-        int spec = kSpecGeneric;
+        int spec = -1;
         bool c_done = true;
         EpiHot h;
         int ri = 0;
@@ -1590,8 +1609,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 break;
             tc_fence_after();
             double nrm = 0.0;
-            // The chunk loop, one copy per product kind (chosen once per tile): the
-            // specialised copies carry no tests of output, C, norm and copy kinds.
+            // The chunk loop, one copy per product kind (epi_spec, chosen once per tile):
+            // the specialised copies carry no tests of output, C, norm and copy kinds.
             auto chunk_loop = [&](auto spec_tag) {
                 using Spec = decltype(spec_tag);
 #pragma unroll 1
@@ -1612,31 +1631,27 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                             cvec = c_load(h, row, (int64_t)tc.tn * BN + nx * 32, full_row(nx), cr);
                         epilogue_finish<NSTG>(h, warp_row0, c0, v, nrm, stage_buf, slot, lane);
                     } else {
-                        if constexpr (Spec::has_c) {
-                            c_apply_bf16(h, cr, cvec, row, c0, rem < 32 ? (int)rem : 32, row_ok, v);
+                        if constexpr (Spec::ckind != C_NONE) {
+                            c_apply_spec<Spec::ckind>(h, cr, cvec, row, c0, rem < 32 ? (int)rem : 32,
+                                                      row_ok, v);
                             if (nx < BN / 32)
-                                cvec = c_load_bf16(h, row, (int64_t)tc.tn * BN + nx * 32, full_row(nx),
-                                                   cr);
+                                cvec = c_load_spec<Spec::ckind>(h, row, (int64_t)tc.tn * BN + nx * 32,
+                                                                full_row(nx), cr);
                         }
-                        epilogue_finish_bf16<NSTG, Spec::sym, Spec::has_t>(h, warp_row0, c0, v,
-                                                                           stage_buf, slot, lane);
+                        epilogue_finish_spec<NSTG, Spec::okind, Spec::sym, Spec::has_t>(
+                            h, warp_row0, c0, v, stage_buf, slot, lane);
                     }
                     ch = nx;
                 }
             };
             switch (spec) {
-            case kSpecSym:
-                chunk_loop(EpiSpec<kSpecSym>{});
-                break;
-            case kSpecSymC:
-                chunk_loop(EpiSpec<kSpecSymC>{});
-                break;
-            case kSpecT:
-                chunk_loop(EpiSpec<kSpecT>{});
-                break;
-            default:
-                chunk_loop(EpiSpec<kSpecGeneric>{});
-                break;
+            case 0: chunk_loop(EpiSpec<0>{}); break;
+            case 1: chunk_loop(EpiSpec<1>{}); break;
+            case 2: chunk_loop(EpiSpec<2>{}); break;
+            case 3: chunk_loop(EpiSpec<3>{}); break;
+            case 4: chunk_loop(EpiSpec<4>{}); break;
+            case 5: chunk_loop(EpiSpec<5>{}); break;
+            default: chunk_loop(EpiSpec<-1>{}); break;
             }
             if (h.norm_acc) {
 #pragma unroll
