@@ -1674,8 +1674,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 tphase ^= 1u;
             }
             if (CHAIN) {
-                // Publish: this warp's part of the tile is in global memory.
-                __threadfence();
+                // Publish: this warp's part of the tile is in global memory. The lanes'
+                // plain stores (diagonal blocks of symmetric products, ragged edges) are
+                // ordered before lane 0's accesses by __syncwarp; lane 0's GPU-scope fence
+                // is cumulative over them and over its TMA stores (waited for and fenced
+                // into the generic proxy), and its counter increment releases them all to
+                // the tiles that acquire the counter.
                 __syncwarp();
                 if (lane == 0) {
                     bulk_wait_all0();
