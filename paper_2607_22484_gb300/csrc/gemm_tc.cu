@@ -1325,6 +1325,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             if (!tc.valid)
                 continue;
             const TcProblem &P = prob_at(L, tc.prob);
+            {
+                // The epilogue reads this problem's fields after o_tma (and the Epi) when
+                // it reaches the tile, a few tiles later: bring their lines into L1 now.
+                const char *pb = reinterpret_cast<const char *>(&P.o_tma);
+                const int nlines =
+                    (int)((sizeof(TcProblem) - offsetof(TcProblem, o_tma) + 127) / 128) + 1;
+                for (int k = 0; k < nlines; ++k)
+                    asm volatile("prefetch.L1 [%0];" ::"l"(pb + 128 * k));
+            }
             // A k-block is one 128-byte swizzle row: 64 BF16 or 128 e4m3 elements.
             const int kshift = P.fp8 ? 7 : 6;
             const int kblocks = (P.K + (1 << kshift) - 1) >> kshift;
