@@ -93,6 +93,40 @@ def quarter_circle_sigma(n: int) -> np.ndarray:
     return np.ascontiguousarray(np.sort(0.5 * (lo + hi))[::-1])
 
 
+def mp_noise_sigma(m: int, n: int, scale: float, count: int) -> np.ndarray:
+    """Singular values of an m x n matrix of N(0, scale^2) entries follow the
+    Marchenko-Pastur law: with y = min/max of the sides and N = the larger side,
+    sigma = scale * sqrt(N * lambda), lambda on [(1 - sqrt y)^2, (1 + sqrt y)^2] with
+    density sqrt((b - lambda)(lambda - a)) / (2 pi y lambda). Returns `count` of its
+    (i - 1/2) / count quantiles, largest first, from the distribution function
+    integrated numerically (lambda = a + (b - a)(1 - cos t) / 2 removes the square-root
+    endpoints; the square case's 1 / sqrt(lambda) edge becomes a finite limit)."""
+    y = min(m, n) / max(m, n)
+    a, b = (1.0 - math.sqrt(y)) ** 2, (1.0 + math.sqrt(y)) ** 2
+    t = np.linspace(0.0, math.pi, 200001)
+    lam = a + (b - a) * (1.0 - np.cos(t)) / 2.0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        f = ((b - a) / 2.0) ** 2 * np.sin(t) ** 2 / (2.0 * math.pi * y * lam)
+    # square case (a = 0): the integrand tends to b / (2 pi y) at lambda = 0
+    f = np.where(lam > 0.0, f, b / (2.0 * math.pi * y))
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (f[1:] + f[:-1]) * np.diff(t))])
+    cdf /= cdf[-1]
+    p = (np.arange(count) + 0.5) / count
+    lam_q = np.interp(p, cdf, lam)
+    return np.ascontiguousarray(np.sort(scale * np.sqrt(max(m, n) * lam_q))[::-1])
+
+
+def low_rank_plus_noise_spectrum(m: int, n: int, rank: int, seed: int, sig_lo: float = 1.0,
+                                 sig_hi: float = 10.0, noise: float = 0.01) -> np.ndarray:
+    """The singular values of ``low_rank_plus_noise``'s recipe for a known-SVD stand-in:
+    `rank` signal values uniform in [sig_lo, sig_hi] and the Marchenko-Pastur quantiles
+    of the N(0, noise^2) part for the rest, largest first."""
+    rng = np.random.default_rng(seed)
+    k = min(m, n)
+    sig = np.concatenate([rng.uniform(sig_lo, sig_hi, rank), mp_noise_sigma(m, n, noise, k - rank)])
+    return np.ascontiguousarray(np.sort(sig)[::-1])
+
+
 def low_rank_plus_noise(m: int, n: int, rank: int, seed: int,
                         sig_lo: float = 1.0, sig_hi: float = 10.0,
                         noise: float = 0.01) -> np.ndarray:
