@@ -500,8 +500,31 @@ def shapes_extra(ctx_cls, pkg, torch, dev):
     for (m, n) in ((8192, 2048), (2048, 8192)):
         a = torch.from_numpy(wl.low_rank_plus_noise(m, n, 64, seed=1003)).to(dev)
         out[f"{m}x{n}_bf16"] = timed(a, 0.5, 20, iters=ITERS, prec="bf16")
+        out[f"{m}x{n}_bf16"]["relerr_known_svd_stand_in"] = _lowrank_stand_in_error(
+            ctx, torch, dev, m, n, 0.5, iters=ITERS, prec="bf16")
         out[f"{m}x{n}_bf16_rank_r"] = timed(a, 0.5, 20, iters=ITERS, prec="bf16", mode="rank_r")
     return out
+
+
+def _lowrank_stand_in_error(ctx, torch, dev, m, n, tau, **opts):
+    """Relative error of the solve on the rectangular recipe's known-SVD stand-in: the 64
+    signal values and the Marchenko-Pastur quantiles of its noise part, Haar singular
+    vectors (exact A_tau without an SVD of the timed matrix)."""
+    import numpy as np
+    import svt_workloads as wl
+    k = min(m, n)
+    sig = wl.low_rank_plus_noise_spectrum(m, n, 64, wl.SEED_LOWRANK)
+    g = torch.Generator(device=dev)
+    g.manual_seed(m + 7 * n)
+    q1 = torch.linalg.qr(torch.randn(m, k, device=dev, dtype=torch.float64, generator=g))[0]
+    q2 = torch.linalg.qr(torch.randn(n, k, device=dev, dtype=torch.float64, generator=g))[0]
+    a = ((q1 * torch.from_numpy(sig).to(dev)) @ q2.T).float()
+    exact = (q1 * torch.from_numpy(np.maximum(sig - tau, 0.0)).to(dev)) @ q2.T
+    y = ctx.polar(a, tau, **opts)
+    torch.cuda.synchronize()
+    err = (torch.linalg.norm(y.double() - exact) / torch.linalg.norm(exact)).item()
+    del a, exact, q1, q2, y
+    return err
 
 
 def svd_context(torch, A, tau, reps=2):
