@@ -317,3 +317,7 @@ def test_serving_large_lane_beside_small_requests():
     print(f"small-request latency median {np.median(lat_small):.2f} ms, large {lat_large}")
     # the small requests submitted behind the long solve finish well before it
     assert np.median(lat_small) < 0.5 * lat_large[0], (np.median(lat_small), lat_large)
+    # the large lane gives its launches to the request with the least work left: the
+    # 2048 x 4096 BF16 request, submitted after the 8192 x 4096 FP32-tier one (about 7x
+    # its work), does not wait for it to finish
+    assert lat_large[1] < lat_large[0], lat_large
