@@ -1,7 +1,10 @@
 // Tensor-core product kernel for sm_103a: D = sum_s L_s R_s^T with BF16
 // operands staged by TMA into 128-byte-swizzled shared memory, tcgen05.mma
 // (kind::f16, BF16 x BF16 -> FP32) accumulating in tensor memory, and a fused
-// epilogue that reads the accumulator back with tcgen05.ld.
+// epilogue that reads the accumulator back with tcgen05.ld. Problems flagged fp8
+// (the FP8 experiment) take e4m3 operands through kind::f8f6f4 instead; the operand
+// kind, like the epilogue's chunk loop (one copy per product kind), is chosen once
+// per tile.
 //
 // This one kernel carries every dense product of the method (Section 2): the
 // shifted Gram A^T A - tau^2 I, the polynomial steps X (a I + b X^T X +
