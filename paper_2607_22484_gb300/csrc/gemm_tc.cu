@@ -1523,9 +1523,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         int buf = 0;
         uint32_t tphase = 0;
         int last_prob = -1;
-        int spec = -1;
         bool c_done = true;
-        EpiHot h;
         int ri = 0;
         uint32_t rphase = 0;
         int hint = 0;
@@ -1590,11 +1588,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             }
             if (PAIR)
                 tc.tm = 2 * tc.tm + (int)rank;  // this CTA's 128-row half of the tile
-            if (tc.prob != last_prob) {
-                load_hot(h, P, calls);
-                spec = epi_spec(h);
-                last_prob = tc.prob;
-            }
+            EpiHot h;  // per tile: its registers are free outside the tile's loops
+            load_hot(h, P, calls);
+            const int spec = epi_spec(h);
+            last_prob = tc.prob;
             const int64_t warp_row0 = (int64_t)tc.tm * kBM + quad * 32;
             const int64_t row = warp_row0 + lane;
             const bool row_ok = row < h.M;
