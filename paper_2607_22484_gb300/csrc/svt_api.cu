@@ -33,6 +33,7 @@
 
 #include "fused_deps.h"
 #include "plan.h"
+#include "segments.h"
 #include "tuning_json.h"
 
 namespace svt {
@@ -1026,30 +1027,13 @@ Segments plan_segments(const Plan &P, double target)
         for (const Op &op : P.ops)
             unit.push_back(op.kind == OP_TC ? P.tc_tensor_flops[op.idx] : 0.0);
     }
-    const int nu = (int)unit.size();
-    if (nu == 0) {
-        seg.bounds = {0, 0};
-        seg.work = {0.0};
-        return seg;
+    seg.bounds = split_units(unit, target, kMaxFusedSegments);
+    for (int k = 0; k + 1 < (int)seg.bounds.size(); ++k) {
+        double w = 0.0;
+        for (int i = seg.bounds[k]; i < seg.bounds[k + 1]; ++i)
+            w += unit[i];
+        seg.work.push_back(w);
     }
-    double total = 0.0;
-    for (double w : unit)
-        total += w;
-    const int want =
-        (int)std::min<double>(kMaxFusedSegments, std::max(1.0, std::ceil(total / std::max(target, 1.0))));
-    const double per = total / want;
-    seg.bounds.push_back(0);
-    seg.work.push_back(0.0);
-    double acc = 0.0;
-    for (int i = 0; i < nu; ++i) {
-        acc += unit[i];
-        seg.work.back() += unit[i];
-        if (acc >= per * (double)seg.bounds.size() && i + 1 < nu && (int)seg.bounds.size() < want) {
-            seg.bounds.push_back(i + 1);
-            seg.work.push_back(0.0);
-        }
-    }
-    seg.bounds.push_back(nu);
     return seg;
 }
 
