@@ -40,6 +40,7 @@
 #include <thread>
 #include <vector>
 
+#include "arena.h"
 #include "plan.h"
 
 using namespace svt;
@@ -89,52 +90,6 @@ double now_ms()
     using namespace std::chrono;
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
-
-// First-fit allocator over [0, size) in kAlign units.
-struct Arena {
-    size_t size = 0;
-    std::map<size_t, size_t> free_;  // offset -> length
-    void reset(size_t s)
-    {
-        size = s;
-        free_.clear();
-        if (s)
-            free_[0] = s;
-    }
-    bool alloc(size_t len, size_t *off)
-    {
-        len = align_up(len, kAlign);
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= len) {
-                *off = it->first;
-                size_t rest = it->second - len;
-                size_t roff = it->first + len;
-                free_.erase(it);
-                if (rest)
-                    free_[roff] = rest;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off, size_t len)
-    {
-        len = align_up(len, kAlign);
-        auto it = free_.emplace(off, len).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-};
 
 struct Request {
     uint64_t ticket = 0;

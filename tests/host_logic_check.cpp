@@ -5,17 +5,25 @@
 //     limit, each within one unit of the even share;
 //   * tuning_to_json / tuning_from_json (tuning_json.h): the autotune cache as JSON --
 //     every written cache reads back identically, and malformed, foreign or
-//     out-of-range text is rejected without changing the output.
+//     out-of-range text is rejected without changing the output;
+//   * Arena (arena.h): the serving loop's first-fit placement of request workspaces --
+//     against a brute-force model of the free ranges, under random alloc / release
+//     sequences: live ranges never overlap and stay inside the arena, each alloc takes
+//     the lowest free range that fits and fails only when none does, free ranges stay
+//     disjoint and coalesced, and releasing everything restores one range.
 //
 // Usage: host_logic_check <seed>; prints "<n> failures" and exits 0 when there are none.
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
+#include <iterator>
 #include <map>
 #include <cstdio>
 #include <random>
 #include <string>
 #include <vector>
 
+#include "arena.h"
 #include "segments.h"
 #include "tuning_json.h"
 
@@ -167,6 +175,74 @@ void check_json(std::mt19937_64 &rng)
     }
 }
 
+void check_arena(std::mt19937_64 &rng)
+{
+    const size_t A = 256;
+    std::uniform_int_distribution<int> ops(50, 400), pick(0, 1 << 30);
+    std::uniform_real_distribution<double> u(0.0, 1.0);
+    for (int trial = 0; trial < 300; ++trial) {
+        svt::Arena ar;
+        const size_t size = A * (1 + pick(rng) % 4096);
+        ar.reset(size);
+        std::map<size_t, size_t> live;  // offset -> rounded length
+        const int nops = ops(rng);
+        for (int op = 0; op < nops; ++op) {
+            if (live.empty() || u(rng) < 0.55) {
+                const size_t len = 1 + (size_t)(u(rng) * u(rng) * (double)size * 0.4);
+                const size_t rl = svt::Arena::round_up(len, A);
+                // the model: free ranges are the gaps between live ranges
+                size_t expect_off = SIZE_MAX, at = 0;
+                for (const auto &kv : live) {
+                    if (kv.first - at >= rl && expect_off == SIZE_MAX)
+                        expect_off = at;
+                    at = kv.first + kv.second;
+                }
+                if (expect_off == SIZE_MAX && size - at >= rl)
+                    expect_off = at;
+                size_t off = 0;
+                const bool ok = ar.alloc(len, &off);
+                expect(ok == (expect_off != SIZE_MAX), "alloc fails only when nothing fits",
+                       (long long)rl, (long long)expect_off);
+                if (ok) {
+                    expect(off == expect_off, "first fit", (long long)off, (long long)expect_off);
+                    expect(off % A == 0 && off + rl <= size, "inside the arena", (long long)off,
+                           (long long)rl);
+                    live[off] = rl;
+                }
+            } else {
+                auto it = live.begin();
+                std::advance(it, pick(rng) % live.size());
+                ar.release(it->first, it->second);
+                live.erase(it);
+            }
+            // live ranges disjoint; free ranges disjoint, coalesced, and the complement
+            size_t prev_end = 0, free_sum = 0, live_sum = 0;
+            for (const auto &kv : live) {
+                expect(kv.first >= prev_end, "live ranges disjoint", (long long)kv.first,
+                       (long long)prev_end);
+                prev_end = kv.first + kv.second;
+                live_sum += kv.second;
+            }
+            size_t fend = 0;
+            bool first = true;
+            for (const auto &kv : ar.free_) {
+                expect(first || kv.first > fend, "free ranges disjoint and coalesced",
+                       (long long)kv.first, (long long)fend);
+                expect(live.find(kv.first) == live.end(), "free range is not live", (long long)kv.first);
+                fend = kv.first + kv.second;
+                free_sum += kv.second;
+                first = false;
+            }
+            expect(free_sum + live_sum == size, "free + live = size", (long long)(free_sum + live_sum),
+                   (long long)size);
+        }
+        for (const auto &kv : live)
+            ar.release(kv.first, kv.second);
+        expect(ar.free_.size() == 1 && ar.free_.begin()->first == 0 && ar.free_.begin()->second == size,
+               "everything released: one range");
+    }
+}
+
 } // namespace
 
 int main(int argc, char **argv)
@@ -174,6 +250,7 @@ int main(int argc, char **argv)
     std::mt19937_64 rng(argc > 1 ? std::strtoull(argv[1], nullptr, 10) : 1);
     check_split(rng);
     check_json(rng);
+    check_arena(rng);
     std::printf("%d failures\n", failures);
     return failures == 0 ? 0 : 1;
 }

@@ -1,8 +1,9 @@
 """Host logic of the library checked on the CPU (tests/host_logic_check.cpp, compiled
 against the library's own headers): how serving's large lane splits a solve's product
-work into launches (segments.h), and the autotune cache's JSON writer and strict reader
-(tuning_json.h). Planting a mistake in either header (no part limit, no format check)
-makes it fail."""
+work into launches (segments.h), the autotune cache's JSON writer and strict reader
+(tuning_json.h), and the serving loop's first-fit workspace placement (arena.h) against
+a brute-force model. Planting a mistake in any of them (no part limit, no format check,
+no merge with the previous free range) makes it fail."""
 import os
 import shutil
 import subprocess
@@ -33,7 +34,7 @@ def checker(tmp_path_factory):
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
-def test_segments_and_tuning_json(checker, seed):
+def test_segments_tuning_json_and_arena(checker, seed):
     r = subprocess.run([checker, str(seed)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.strip().endswith("0 failures"), r.stdout
